@@ -1,0 +1,239 @@
+"""ctypes wrapper of the FP64 CPU oracle (npfem_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py, never by the product package.
+
+Arrays are float64, AoS [n, 3] per cell (or [cells, n, 3] for batches).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "npfem_oracle.c")
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD_DIR, "libnpfem_oracle.so")
+
+MATERIAL_ORDER = ("B", "C", "D", "k_bend", "k_vol", "k_mat_hess", "density", "alpha_D", "beta_D", "kappa")
+STATUS = {0: "OK", 1: "MAXITER", 2: "LINESEARCH_FAIL", 3: "NONFINITE"}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no fast-math)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, SRC, "-lm", "-lpthread"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class Opts(C.Structure):
+    _fields_ = [("lbfgs_m", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double), ("c1", C.c_double),
+                ("c2", C.c_double), ("max_halvings", C.c_int), ("fixed_alpha", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("evaluations", C.c_int), ("status", C.c_int), ("pad", C.c_int),
+                ("residual", C.c_double), ("objective", C.c_double), ("volume", C.c_double), ("area", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.c_void_p
+        dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+        ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        L.or_create.restype = P
+        L.or_create.argtypes = [C.c_int, C.c_int, ip, dp, dp, C.c_double, C.c_int]
+        L.or_destroy.argtypes = [P]
+        L.or_rest_info.argtypes = [P, dp]
+        for name in ("or_masses", "or_voronoi", "or_laplacian", "or_hessian", "or_apply_hinv"):
+            getattr(L, name).argtypes = [P, dp]
+        L.or_sl2_project.restype = C.c_double
+        L.or_sl2_project.argtypes = [C.c_double, C.c_double]
+        for name in ("or_skalak_f", "or_skalak_fp"):
+            getattr(L, name).restype = C.c_double
+            getattr(L, name).argtypes = [C.c_double, C.c_double, C.c_double]
+        for name in ("or_energy_area", "or_energy_skalak"):
+            getattr(L, name).restype = C.c_double
+            getattr(L, name).argtypes = [P, dp, P, P]
+        L.or_energy_bend.restype = C.c_double
+        L.or_energy_bend.argtypes = [P, dp, P]
+        L.or_energy_vol.restype = C.c_double
+        L.or_energy_vol.argtypes = [P, dp, P, P]
+        L.or_volume.restype = C.c_double
+        L.or_volume.argtypes = [P, dp]
+        L.or_area.restype = C.c_double
+        L.or_area.argtypes = [P, dp]
+        L.or_volume_gradient.argtypes = [P, dp, dp]
+        L.or_objective.restype = C.c_double
+        L.or_objective.argtypes = [P, dp, dp, P, P, P]
+        L.or_internal_energy.restype = C.c_double
+        L.or_internal_energy.argtypes = [P, dp, P]
+        L.or_first_guess.argtypes = [P, dp, dp, dp, dp]
+        L.or_residual.restype = C.c_double
+        L.or_residual.argtypes = [P, dp]
+        L.or_solve.restype = C.c_int
+        L.or_solve.argtypes = [P, dp, dp, C.POINTER(Opts), C.POINTER(Stats)]
+        L.or_post_step.argtypes = [P, dp, dp, C.c_double]
+        L.or_step.restype = C.c_int
+        L.or_step.argtypes = [P, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats)]
+        L.or_step_batch.restype = C.c_int
+        L.or_step_batch.argtypes = [P, C.c_int, C.c_int, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats), C.c_int]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def make_opts(lbfgs_m=5, max_iter=50, tol=1e-6, c1=1e-4, c2=0.9, max_halvings=30, fixed_alpha=0) -> Opts:
+    return Opts(lbfgs_m, max_iter, tol, c1, c2, max_halvings, fixed_alpha)
+
+
+def sl2_project(s1: float, s2: float) -> float:
+    return lib().or_sl2_project(float(s1), float(s2))
+
+
+def skalak_f(l, B, D):
+    return lib().or_skalak_f(float(l), float(B), float(D))
+
+
+def skalak_fp(l, B, D):
+    return lib().or_skalak_fp(float(l), float(B), float(D))
+
+
+class Model:
+    """One mesh topology with its rest shape, material and time step."""
+
+    def __init__(self, rest: np.ndarray, tris: np.ndarray, material: np.ndarray, dt: float, equal_mass: bool = False):
+        L = lib()
+        self.rest = np.ascontiguousarray(rest, dtype=np.float64)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32)
+        self.material = np.ascontiguousarray(material, dtype=np.float64)
+        self.dt = float(dt)
+        self.n = self.rest.shape[0]
+        self._h = L.or_create(self.n, self.tris.shape[0], self.tris, self.rest, self.material, self.dt, int(equal_mass))
+        if not self._h:
+            raise ValueError("oracle rejected the mesh (not a closed oriented manifold, or H~ not SPD)")
+        info = np.zeros(4)
+        L.or_rest_info(self._h, info)
+        self.V0, self.A0, self.lbar, self.mtotal = info
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.or_destroy(self._h)
+            self._h = None
+
+    # --- queries -----------------------------------------------------------------
+    def masses(self):
+        o = np.zeros(self.n); lib().or_masses(self._h, o); return o
+
+    def voronoi(self):
+        o = np.zeros(self.n); lib().or_voronoi(self._h, o); return o
+
+    def laplacian(self):
+        o = np.zeros((self.n, self.n)); lib().or_laplacian(self._h, o); return o
+
+    def hessian(self):
+        o = np.zeros((self.n, self.n)); lib().or_hessian(self._h, o); return o
+
+    def apply_hinv(self, b):
+        b = np.array(b, dtype=np.float64, order="C"); lib().or_apply_hinv(self._h, b); return b
+
+    # --- energies ------------------------------------------------------------------
+    def _energy(self, fn, x, with_grad=True):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        g = np.zeros_like(x) if with_grad else None
+        bad = C.c_int(0)
+        e = fn(self._h, x, _ptr(g), C.byref(bad))
+        return e, g
+
+    def energy_area(self, x):
+        return self._energy(lib().or_energy_area, x)
+
+    def energy_skalak(self, x):
+        return self._energy(lib().or_energy_skalak, x)
+
+    def energy_bend(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        g = np.zeros_like(x)
+        return lib().or_energy_bend(self._h, x, _ptr(g)), g
+
+    def energy_vol(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        g = np.zeros_like(x)
+        V = C.c_double(0)
+        e = lib().or_energy_vol(self._h, x, _ptr(g), C.byref(V))
+        return e, g
+
+    def volume(self, x):
+        return lib().or_volume(self._h, np.ascontiguousarray(x, dtype=np.float64))
+
+    def area(self, x):
+        return lib().or_area(self._h, np.ascontiguousarray(x, dtype=np.float64))
+
+    def volume_gradient(self, x):
+        o = np.zeros((self.n, 3)); lib().or_volume_gradient(self._h, np.ascontiguousarray(x, dtype=np.float64), o); return o
+
+    def objective(self, x, y):
+        """g(x) and grad g(x); parts = (inertia, area, skalak, bend, volume energy, V)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        g = np.zeros_like(x)
+        parts = np.zeros(6)
+        bad = C.c_int(0)
+        e = lib().or_objective(self._h, x, y, _ptr(g), _ptr(parts), C.byref(bad))
+        return e, g, parts
+
+    def internal_energy(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        g = np.zeros_like(x)
+        return lib().or_internal_energy(self._h, x, _ptr(g)), g
+
+    def first_guess(self, x, v, f):
+        y = np.zeros((self.n, 3))
+        lib().or_first_guess(self._h, *(np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, f)), y)
+        return y
+
+    def residual(self, grad):
+        return lib().or_residual(self._h, np.ascontiguousarray(grad, dtype=np.float64))
+
+    def solve(self, x0, y, opts: Opts | None = None):
+        x = np.array(x0, dtype=np.float64, order="C")
+        st = Stats()
+        lib().or_solve(self._h, x, np.ascontiguousarray(y, dtype=np.float64), C.byref(opts or make_opts()), C.byref(st))
+        return x, st
+
+    def post_step(self, x, v, kappa):
+        v = np.array(v, dtype=np.float64, order="C")
+        lib().or_post_step(self._h, np.ascontiguousarray(x, dtype=np.float64), v, float(kappa))
+        return v
+
+    def step(self, x, v, f, opts: Opts | None = None):
+        """One time step of one cell; returns (x_{n+1}, v_{n+1}, stats)."""
+        x = np.array(x, dtype=np.float64, order="C")
+        v = np.array(v, dtype=np.float64, order="C")
+        st = Stats()
+        lib().or_step(self._h, x, v, np.ascontiguousarray(f, dtype=np.float64), C.byref(opts or make_opts()), C.byref(st))
+        return x, v, st
+
+    def step_batch(self, x, v, f, opts: Opts | None = None, steps: int = 1, threads: int = 1):
+        """steps time steps of every cell of [cells, n, 3] arrays (the same force each step)."""
+        x = np.array(x, dtype=np.float64, order="C")
+        v = np.array(v, dtype=np.float64, order="C")
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        cells = x.shape[0]
+        st = (Stats * cells)()
+        lib().or_step_batch(self._h, cells, steps, x, v, f, C.byref(opts or make_opts()), st, threads)
+        return x, v, list(st)
