@@ -1,0 +1,341 @@
+"""Benchmark of the npFEM time step on GB300: RBC-steps/s on 642-vertex cells.
+
+Workload (default): 1024 red-blood-cell membranes of the 642-vertex / 1280-triangle
+discocyte mesh, randomly rotated and translated in a 100 um cube, shear-flow
+traction (rate U(10, 1000) 1/s) plus N(0, 0.5 pN) noise, dt = 0.1 us, residual
+tolerance 1e-6.  One "step" is one npfem_step call advancing every cell by one
+time step (Algorithm 1: first guess, quasi-Newton solve, velocity update,
+post-convergence dissipation).
+
+Legs:
+  value     device time of npfem_step with the state resident in HBM (CUDA events on
+            the launch stream, L2 flushed between steps because the state fits in L2)
+  e2e       the same through npfem_step_host: pinned host buffers copied in and out
+            inside the timed region
+  plain     the plain FP32 GPU path (FP32 SIMT contraction, first-guess warm start)
+  cpu_baseline / --impl reference
+            the FP64 CPU oracle on this machine's cores, on a bounded sample
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--cells C]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RBC-steps/s (642-vtx cells, equal accuracy), chosen vs plain form, % roofline"
+DT = 0.1
+N_VERTS = 642
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cells", type=int, default=1024)
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(n, m, stats_iters, stats_evals, cells):
+    """Per-launch algorithmic bytes of the step (FP32): per cell 5*12n for x_n, v_n,
+    F_ext in and x, v out; per iteration (4m + 6)*12n (the L-BFGS history streamed
+    twice, plus x, grad, d reads and s, y, x writes); per evaluation 2*12n."""
+    vb = 12 * n
+    return cells * 5 * vb + stats_iters * (4 * m + 6) * vb + stats_evals * 2 * vb
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------------
+# CPU oracle (reported baseline; also the reference arm)
+# ----------------------------------------------------------------------------------
+def oracle_sample(pop, cells, steps, threads):
+    from oracle import oracle as O
+    from paper_1903_06479_gb300 import workloads as W
+    m = O.Model(pop["rest"], pop["tris"], W.material_vector(), DT)
+    x = pop["x"][:cells].astype(np.float32).astype(np.float64)
+    v = pop["v"][:cells].astype(np.float32).astype(np.float64)
+    f = pop["f"][:cells].astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    m.step_batch(x, v, f, O.make_opts(tol=1e-6, max_iter=50), steps=steps, threads=threads)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank, world, local, pg = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    from paper_1903_06479_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    pop = W.population(N_VERTS, cores, seed=1, forces="shear", noise_pN=0.5)
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(pop, cores, 1, cores)
+    total = 0.0
+    for _ in range(args.steps):
+        total += oracle_sample(pop, cores, 1, cores)
+    value = cores * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RBC-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{cores} x 642-vertex RBCs per step (sample of the 1024-cell shear-flow "
+                                   f"population), tol 1e-6, dt 0.1 us"},
+            "cpu_baseline": {"value": value, "unit": "RBC-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} cells x 1 time step per timed step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": "RBC-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------
+# GPU legs
+# ----------------------------------------------------------------------------------
+def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush):
+    xs = torch.tensor(W.to_soa(pop["x"][:cells]), dtype=torch.float32, device="cuda")
+    vs = torch.tensor(W.to_soa(pop["v"][:cells]), dtype=torch.float32, device="cuda")
+    fs = torch.tensor(W.to_soa(pop["f"][:cells]), dtype=torch.float32, device="cuda")
+    st = torch.zeros((cells, 32), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    iters = evals = 0
+    statuses = np.zeros(4, dtype=np.int64)
+    res_max = 0.0
+    for k in range(steps):
+        flush.zero_()  # writes a buffer larger than L2 between timed steps
+        ev[k][0].record(stream)
+        N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
+        ev[k][1].record(stream)
+        if k == steps - 1 or k % 50 == 0:
+            s = st.cpu().numpy().view(N.CELL_STATS_DTYPE).reshape(cells)
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in ev]
+    # statistics of the last step (per-launch work for the roofline)
+    s = st.cpu().numpy().view(N.CELL_STATS_DTYPE).reshape(cells)
+    iters, evals = int(s["iterations"].sum()), int(s["evaluations"].sum())
+    for q in range(4):
+        statuses[q] = int((s["status"] == q).sum())
+    res_max = float(s["residual"].max())
+    return times, iters, evals, statuses, res_max
+
+
+def e2e_leg(N, W, handle, pop, cells, steps, warmup, torch):
+    x = torch.tensor(W.to_soa(pop["x"][:cells]), dtype=torch.float32).pin_memory()
+    v = torch.tensor(W.to_soa(pop["v"][:cells]), dtype=torch.float32).pin_memory()
+    f = torch.tensor(W.to_soa(pop["f"][:cells]), dtype=torch.float32).pin_memory()
+    stats = torch.zeros((cells, 32), dtype=torch.uint8).pin_memory()
+    xa, va, fa, sa = x.numpy(), v.numpy(), f.numpy(), stats.numpy()
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        handle.step_host(xa, va, fa, sa.view(N.CELL_STATS_DTYPE).reshape(cells), stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        handle.step_host(xa, va, fa, sa.view(N.CELL_STATS_DTYPE).reshape(cells), stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nb = 4 * 3 * N_VERTS * cells
+    return dt, 3 * nb, 2 * nb + 32 * cells
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_1903_06479_gb300 import npfem as N
+    from paper_1903_06479_gb300 import workloads as W
+    N.lib()
+    cells = args.cells
+    pop = W.population(N_VERTS, cells, seed=1 + rank, forces="shear", noise_pN=0.5)
+    opts = N.default_opts(precision=args.precision, tol=1e-6, max_iter=50)
+    handle = N.Handle(pop["rest"], pop["tris"], N.material(), opts, dt=DT, device=local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    barrier(pg)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        times, iters, evals, statuses, res_max = device_leg(N, W, handle, pop, cells, args.steps, args.warmup,
+                                                            torch, flush)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier(pg)
+    dev_s = sum(times) / 1e3
+    dev_s_max = max_over_ranks(pg, dev_s)
+    total_cells = sum_over_ranks(pg, cells)
+    value = total_cells * args.steps / dev_s_max
+    clocks = clk.summary()
+
+    plain = None
+    if not args.no_plain and args.precision != "fp32":
+        hp = N.Handle(pop["rest"], pop["tris"], N.material(), N.default_opts(precision="fp32"), dt=DT, device=local)
+        tp, _, _, _, _ = device_leg(N, W, hp, pop, cells, max(10, args.steps // 4), 2, torch, flush)
+        plain = {"value": max_over_ranks(pg, 0) or total_cells * len(tp) / (sum(tp) / 1e3), "unit": "RBC-steps/s",
+                 "precision": "fp32"}
+
+    e2e = None
+    if not args.no_e2e:
+        barrier(pg)
+        e_s, bi, bo = e2e_leg(N, W, handle, pop, cells, max(5, args.steps // 4), 2, torch)
+        e_s = max_over_ranks(pg, e_s)
+        e2e = {"value": total_cells * max(5, args.steps // 4) / e_s, "unit": "RBC-steps/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+    pk, pk_kind = peaks()
+    m = opts.lbfgs_m
+    alg = algorithmic_bytes(N_VERTS, m, iters, evals, cells)
+    t_launch = dev_s / args.steps
+    achieved = alg / t_launch / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind,
+            "kernel": "cell_kernel<float>", "algorithmic_bytes_per_launch": alg}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        sample_cells = min(64, cells)
+        t = oracle_sample(pop, sample_cells, 10, cores)
+        cpu = {"value": sample_cells * 10 / t, "unit": "RBC-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{sample_cells} cells x 10 time steps of the same workload, FP64, {cores} threads"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "RBC-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+                "data": "synthetic",
+                "config": {"workload": f"{cells} RBCs x 642-vertex discocyte per GPU, shear traction U(10,1000)/s "
+                                       f"+ N(0,0.5 pN), dt 0.1 us, tol 1e-6",
+                           "cells_per_gpu": cells, "precision": args.precision, "lbfgs_m": m,
+                           "l2": "flushed between timed steps (256 MB write)"},
+                "gpu_launches": args.steps,
+                "wall_s": t_wall,
+                "per_step_ms": {"median": float(np.median(times)), "min": float(np.min(times)),
+                                "max": float(np.max(times))},
+                "solver": {"iterations_per_cell": iters / cells, "evaluations_per_cell": evals / cells,
+                           "status_counts": statuses.tolist(), "residual_max": res_max},
+                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "plain": plain}
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

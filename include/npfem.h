@@ -1,0 +1,181 @@
+/*
+ * npfem.h -- C ABI of libnpfem.so, the GB300 (sm_103a) npFEM red-blood-cell solver.
+ *
+ * The library advances many triangulated red-blood-cell membranes by one implicit
+ * time step each (Kotsalos, Latt & Chopard, arXiv:1903.06479, Algorithm 1): first
+ * guess y_n (Eq. preOptimizationNewton), minimisation of the objective g of
+ * Eq. (GeneralizedObjectiveFunction) by L-BFGS with the constant initial matrix
+ * H~ = M~/h^2 + L (Sec. 2.1.1) and a backtracking line search, then
+ * v_{n+1} = (x_{n+1} - x_n)/h and the post-convergence dissipation of Sec. 2.1.4.
+ * Energies: local area preservation and bending (projective, Sec. 2.1.2), global
+ * volume conservation (Sec. 2.1.2), modified Skalak strain energy (Sec. 2.1.3).
+ *
+ * Units: um, us, pN (mass unit pN us^2/um; energy pN um).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value 0 on success, a negative NPFEM_ERR_* code on failure; the
+ *     message of the last failure on the calling thread is npfem_last_error().
+ *   - Cell state is component-major SoA: for cell c of a mesh with n vertices,
+ *     x[c][0..2][0..n-1] (the x, y and z rows), contiguous, cells back to back.
+ *     Several meshes (groups) in one call are concatenated in argument order.
+ *   - "device" pointers are CUDA global-memory pointers on the handle's device,
+ *     owned by the caller; "host" pointers are CPU memory owned by the caller
+ *     (pinned memory gives the fastest copies).
+ *   - Per-cell non-convergence is not a call error: it is reported in the
+ *     optional npfem_cell_stats array.
+ */
+#ifndef NPFEM_H
+#define NPFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes -------------------------------------------------------- */
+#define NPFEM_OK 0
+#define NPFEM_ERR_INVALID_ARG (-1) /* a pointer, size or option is out of range        */
+#define NPFEM_ERR_BAD_MESH (-2)    /* not a closed, consistently oriented 2-manifold,  */
+                                   /* or a degenerate rest triangle                    */
+#define NPFEM_ERR_CUDA (-3)        /* a CUDA runtime call failed (message has details) */
+#define NPFEM_ERR_OOM (-4)         /* device allocation failed                          */
+#define NPFEM_ERR_TIMEOUT (-5)     /* a bounded device wait gave up                      */
+#define NPFEM_ERR_NOT_SPD (-6)     /* H~ lost positive definiteness during inversion    */
+
+/* ---- per-cell status (npfem_cell_stats.status) ---------------------------- */
+#define NPFEM_CELL_OK 0              /* residual <= tol                                 */
+#define NPFEM_CELL_MAXITER 1         /* iteration cap reached; last accepted iterate kept */
+#define NPFEM_CELL_LINESEARCH_FAIL 2 /* no step length passed the Armijo test          */
+#define NPFEM_CELL_NONFINITE 3       /* NaN/Inf met; x_n kept, v set to zero            */
+
+/* ---- precision of the solve (npfem_opts.precision) ----------------------- */
+#define NPFEM_PREC_FP64 0 /* state, energies and the A^-1 contraction in FP64            */
+#define NPFEM_PREC_FP32 1 /* state and energies FP32 (sums FP64), A^-1 FP32 on the SIMT  */
+                          /* pipes: the plain GPU path                                  */
+#define NPFEM_PREC_TF32 2 /* as FP32, A^-1 contraction on tcgen05 tensor cores in TF32    */
+                          /* with FP32 accumulation plus one refinement sweep           */
+#define NPFEM_PREC_BF16 3 /* as TF32 but BF16 operands                                   */
+
+typedef struct npfem_handle npfem_handle;
+
+/* Closed triangle mesh of one cell topology with its rest shape (host memory).
+   tris: [n_tris][3] vertex indices, counter-clockwise seen from outside.
+   rest_xyz: [n_verts][3] rest positions in um (AoS). Copied by npfem_create. */
+typedef struct {
+    int32_t n_verts, n_tris;
+    const int32_t* tris;
+    const double* rest_xyz;
+} npfem_mesh;
+
+/* Material (parameter table of the results section; Sec. 2.1.2-2.1.4).
+   B, D: Skalak shear modulus and strain-hardening term (pN/um), Sec. 2.1.3.
+   C: area-preservation stiffness (pN/um), weight w_i = C * rest area.
+   k_bend: bending stiffness (pN um), weight k_bend * Voronoi area.
+   k_vol: volume-conservation weight (pN/um).
+   k_mat_hess: stiffness of the optional material term added to L (Sec. 2.1.1,
+               "non-PD contribution to the Hessian"); 0 disables it.
+   density: mass per rest volume (pN us^2 / um^4); total mass = density * V0.
+   alpha_D, beta_D: Rayleigh damping C = alpha_D M + beta_D L (beta_D in us).
+   kappa: post-convergence damping coefficient in [0, 1]. */
+typedef struct {
+    double B, C, D, k_bend, k_vol, k_mat_hess, density, alpha_D, beta_D, kappa;
+} npfem_material;
+
+/* Solver options.
+   precision: NPFEM_PREC_*.
+   lbfgs_m: L-BFGS history window (0..8; 0 = preconditioned descent with H~^-1).
+   max_iter: cap on quasi-Newton iterations per step (>= 0).
+   tol: stopping residual r = RMS_i(h^2 |grad_i g| / m_i) / mean rest edge length.
+   c1: Armijo constant; c2: curvature constant gating the history update.
+   max_halvings: line-search trials after alpha = 1 (0..60).
+   fixed_alpha: 1 = always take alpha = 1 (the local/global solver of Appendix A).
+   equal_mass: 1 = lump the mass equally, 0 = by barycentric rest area.
+   armijo_noise: multiple of the estimated rounding error of g added to the
+                 Armijo bound (FP32 energies); 0 = exact test. */
+typedef struct {
+    int32_t precision;
+    int32_t lbfgs_m;
+    int32_t max_iter;
+    double tol;
+    double c1, c2;
+    int32_t max_halvings;
+    int32_t fixed_alpha;
+    int32_t equal_mass;
+    double armijo_noise;
+} npfem_opts;
+
+/* Per-cell result of one npfem_step call (device memory, 32 bytes). */
+typedef struct {
+    int32_t iterations;  /* accepted quasi-Newton iterations                 */
+    int32_t evaluations; /* objective/gradient evaluations                    */
+    int32_t status;      /* NPFEM_CELL_*                                      */
+    float residual;      /* final r                                           */
+    double objective;    /* final g                                           */
+    double volume;       /* enclosed volume at x_{n+1} (um^3)                  */
+} npfem_cell_stats;
+
+/* Fills *o with the defaults used throughout the library: FP32, m = 5,
+   max_iter = 50, tol = 1e-6, c1 = 1e-4, c2 = 0.9, 30 halvings, area-lumped mass,
+   armijo_noise = 4. */
+void npfem_default_opts(npfem_opts* o);
+
+/* Creates a handle for one mesh topology on CUDA device `device` and time step dt
+   (us): validates the mesh, computes the rest-state tables in FP64 on the host
+   (D_m^-1, rest areas, cotangent weights, mixed Voronoi areas, lumped masses, L),
+   inverts H~ = M~/h^2 + L in FP64 on the GPU (the one-time prefactorisation of
+   Sec. 2.1.1) and keeps A^-1 = H~^-1 resident in the precision of opts->precision.
+   The handle owns all its device memory. Blocks until the setup is complete.
+   Errors: INVALID_ARG (null pointers, bad sizes/options, dt <= 0), BAD_MESH,
+   NOT_SPD, OOM, CUDA. */
+int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_opts* opts, double dt, int device,
+                 npfem_handle** out);
+
+/* Releases the handle and its device memory (synchronises its device). */
+int npfem_destroy(npfem_handle* h);
+
+/* Advances every cell of n_groups meshes by one time step (Algorithm 1), in one
+   kernel launch on `stream` (a cudaStream_t; 0 = legacy default stream).
+   meshes[g] and cells_per_group[g] (host arrays) name each group; all handles must
+   share device, precision and dt.
+   x, v: device SoA state (float, or double for NPFEM_PREC_FP64), updated in place
+   to x_{n+1}, v_{n+1}. f_ext: device SoA external forces (pN), read only.
+   dt must equal the handle's dt (a new dt needs a new handle).
+   stats: optional device array of sum(cells_per_group) records, or NULL.
+   Asynchronous with respect to the host. The library-owned scratch (L-BFGS history
+   of large meshes) is per handle set; calls that share handles must be ordered on
+   one stream. Errors: INVALID_ARG, CUDA. */
+int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
+               const void* f_ext, double dt, void* stream, npfem_cell_stats* stats);
+
+/* Same as npfem_step for one handle with HOST buffers: copies x, v, f_ext (host,
+   SoA, same element type) to library-owned device buffers, steps, and copies x, v
+   and (if stats_host != NULL) the per-cell stats back; returns after the copies
+   completed. Errors as npfem_step, plus OOM. */
+int npfem_step_host(npfem_handle* h, int n_cells, void* x_host, void* v_host, const void* f_host, double dt,
+                    void* stream, npfem_cell_stats* stats_host);
+
+/* Evaluates the objective g and its gradient (Eq. GeneralizedObjectiveFunction and
+   its derivative) for n_cells cells of one handle at positions x with inertia
+   target y (device SoA). Writes grad (device SoA) and, per cell, 8 doubles to
+   parts (device): inertia, area, Skalak, bending, volume energies, enclosed
+   volume, total g, residual r. Used to check the energy kernels one by one.
+   Errors: INVALID_ARG, CUDA. */
+int npfem_eval(npfem_handle* h, int n_cells, const void* x, const void* y, void* grad, double* parts, void* stream);
+
+/* Copies the handle's FP64 A^-1 (n_verts x n_verts, row-major) to host memory.
+   Errors: INVALID_ARG, CUDA. */
+int npfem_get_inverse(npfem_handle* h, double* out_host);
+
+/* Copies per-vertex lumped masses (n_verts doubles) and the scalars
+   {V0, A0, mean rest edge length, total mass} (4 doubles) to host memory. */
+int npfem_get_rest_info(npfem_handle* h, double* masses_host, double* scalars_host);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* npfem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPFEM_H */

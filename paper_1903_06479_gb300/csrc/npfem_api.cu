@@ -1,0 +1,512 @@
+// C ABI of libnpfem.so (declared in include/npfem.h): handle set-up, placement of the
+// per-cell solver vectors in shared or global memory, and the launches.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "npfem_internal.h"
+
+using namespace npfem;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define NPFEM_CUDA(call)                                                                               \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? NPFEM_ERR_OOM : NPFEM_ERR_CUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct npfem_handle {
+    int device = 0;
+    int precision = NPFEM_PREC_FP32;
+    double dt = 0.0;
+    npfem_opts opts{};
+    npfem_material mat{};
+    HostTopo host;
+    int n = 0, nt = 0, n_pad = 0;
+    std::vector<void*> allocs;  // every device allocation owned by the handle
+    TopoDev<float> tf{};
+    TopoDev<double> td{};
+    double* ainv64 = nullptr;   // n x n FP64 inverse (unpadded)
+    // launch resources (used when this handle is the first of a step call)
+    unsigned int* work = nullptr;
+    char* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int sm_count = 0, smem_optin = 0;
+    int threads = 512;
+    // buffers of npfem_step_host
+    void* hx = nullptr;
+    void* hv = nullptr;
+    void* hf = nullptr;
+    npfem_cell_stats* hstats = nullptr;
+    size_t host_cells = 0;
+    std::mutex mu;
+
+    template <typename X>
+    X* alloc(size_t count, int* err)
+    {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(X) + 16);
+        if (e != cudaSuccess) {
+            *err = fail(e == cudaErrorMemoryAllocation ? NPFEM_ERR_OOM : NPFEM_ERR_CUDA,
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return nullptr;
+        }
+        allocs.push_back(p);
+        return static_cast<X*>(p);
+    }
+    void release()
+    {
+        for (void* p : allocs) cudaFree(p);
+        allocs.clear();
+        if (scratch) cudaFree(scratch);
+        scratch = nullptr;
+        scratch_bytes = 0;
+        if (hx) cudaFree(hx);
+        if (hv) cudaFree(hv);
+        if (hf) cudaFree(hf);
+        if (hstats) cudaFree(hstats);
+        hx = hv = hf = nullptr;
+        hstats = nullptr;
+    }
+};
+
+namespace {
+
+template <typename X, typename S>
+int upload(npfem_handle* h, const std::vector<S>& src, const X** out)
+{
+    int err = 0;
+    std::vector<X> tmp(src.size());
+    for (size_t i = 0; i < src.size(); ++i) tmp[i] = (X)src[i];
+    X* d = h->alloc<X>(std::max<size_t>(tmp.size(), 1), &err);
+    if (!d) return err;
+    if (!tmp.empty()) NPFEM_CUDA(cudaMemcpy(d, tmp.data(), tmp.size() * sizeof(X), cudaMemcpyHostToDevice));
+    *out = d;
+    return 0;
+}
+
+template <typename T>
+int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv)
+{
+    const HostTopo& H = h->host;
+    int rc;
+    std::vector<unsigned short> tri4(4 * (size_t)H.nt, 0);
+    for (int t = 0; t < H.nt; ++t)
+        for (int a = 0; a < 3; ++a) tri4[4 * t + a] = (unsigned short)H.tri[3 * t + a];
+    const unsigned short* dtri = nullptr;
+    if ((rc = upload(h, tri4, &dtri))) return rc;
+    tp->tri = reinterpret_cast<const ushort4*>(dtri);
+    if ((rc = upload(h, H.dminv, &tp->dminv))) return rc;
+    if ((rc = upload(h, H.W, &tp->W))) return rc;
+    if ((rc = upload(h, H.mass, &tp->mass))) return rc;
+    std::vector<double> inv_m(H.n);
+    for (int i = 0; i < H.n; ++i) inv_m[i] = 1.0 / H.mass[i];
+    if ((rc = upload(h, inv_m, &tp->inv_mass))) return rc;
+    if ((rc = upload(h, H.bend_w, &tp->bend_w))) return rc;
+    if ((rc = upload(h, H.dg_norm, &tp->dg_norm))) return rc;
+    if ((rc = upload(h, H.csum, &tp->csum))) return rc;
+    if ((rc = upload(h, H.nsign, &tp->nsign))) return rc;
+    if ((rc = upload(h, H.ring_ptr, &tp->ring_ptr))) return rc;
+    std::vector<unsigned short> ridx(H.ring_idx.begin(), H.ring_idx.end());
+    if ((rc = upload(h, ridx, &tp->ring_idx))) return rc;
+    if ((rc = upload(h, H.ring_c, &tp->ring_c))) return rc;
+    tp->n = H.n;
+    tp->nt = H.nt;
+    tp->n_pad = h->n_pad;
+    tp->nnz = (int)H.ring_idx.size();
+    tp->ainv = static_cast<const T*>(ainv);
+    tp->ainv_lp = nullptr;
+    tp->h_ptr = nullptr;
+    tp->h_idx = nullptr;
+    tp->h_val = nullptr;
+    tp->C = (T)h->mat.C;
+    tp->B = (T)h->mat.B;
+    tp->Dsk = (T)h->mat.D;
+    tp->kvol = (T)h->mat.k_vol;
+    tp->h = (T)h->dt;
+    tp->inv_h2 = (T)(1.0 / (h->dt * h->dt));
+    tp->inertia_scale = (T)(1.0 + h->dt * h->mat.alpha_D);
+    tp->kappa = (T)h->mat.kappa;
+    tp->lbar = (T)H.lbar;
+    tp->inv_lbar = (T)(1.0 / H.lbar);
+    tp->V0 = H.V0;
+    return 0;
+}
+
+int check_opts(const npfem_opts* o)
+{
+    if (o->precision < NPFEM_PREC_FP64 || o->precision > NPFEM_PREC_BF16)
+        return fail(NPFEM_ERR_INVALID_ARG, "opts.precision must be one of NPFEM_PREC_*");
+    if (o->lbfgs_m < 0 || o->lbfgs_m > kMaxHistory)
+        return fail(NPFEM_ERR_INVALID_ARG, "opts.lbfgs_m must be in 0..8");
+    if (o->max_iter < 0 || o->max_halvings < 0 || o->max_halvings > 60)
+        return fail(NPFEM_ERR_INVALID_ARG, "opts.max_iter must be >= 0 and max_halvings in 0..60");
+    if (!(o->tol >= 0.0) || !(o->c1 > 0.0 && o->c1 < 1.0) || !(o->c2 > o->c1 && o->c2 < 1.0) ||
+        !(o->armijo_noise >= 0.0))
+        return fail(NPFEM_ERR_INVALID_ARG, "opts: need tol >= 0, 0 < c1 < c2 < 1, armijo_noise >= 0");
+    return 0;
+}
+
+// Places the per-cell vectors: shared memory in priority order while it fits, the
+// rest in a per-block global slot.  Returns the smem bytes (after kFixedSmem).
+template <typename T>
+void place_vectors(GroupDesc<T>* g, int n_pad, int m, int smem_budget, long long* slot_bytes)
+{
+    const int vb = 3 * n_pad * (int)sizeof(T);
+    int order[kMaxVecs], nv = 0;
+    const int base[kNumBaseVecs] = {V_XN, V_U, V_UT, V_G, V_GT, V_GC, V_UY, V_D};
+    for (int q = 0; q < kNumBaseVecs; ++q) order[nv++] = base[q];
+    for (int q = 0; q < m; ++q) {
+        order[nv++] = V_SBASE + q;
+        order[nv++] = V_SBASE + m + q;
+    }
+    int used = 0;
+    long long gl = 0;
+    for (int q = 0; q < kMaxVecs; ++q) g->loc[q] = 0;
+    for (int q = 0; q < nv; ++q) {
+        if (used + vb <= smem_budget) {
+            g->loc[order[q]] = used;
+            used += vb;
+        } else {
+            g->loc[order[q]] = -(int)gl - 1;
+            gl += vb;
+        }
+    }
+    g->smem_bytes = used;
+    *slot_bytes = gl;
+}
+
+template <typename T>
+int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T* x, T* v, const T* f, const T* y,
+              T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream)
+{
+    npfem_handle* h0 = meshes[0];
+    LaunchArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    long long total = 0, state = 0, slot = 0;
+    int smem_max = 0;
+    const int budget = h0->smem_optin - kFixedSmem - 1024;
+    for (int gi = 0; gi < n_groups; ++gi) {
+        npfem_handle* h = meshes[gi];
+        GroupDesc<T>& g = a.g[gi];
+        g.topo = *reinterpret_cast<const TopoDev<T>*>(sizeof(T) == 4 ? (const void*)&h->tf : (const void*)&h->td);
+        g.cell_begin = total;
+        g.state_off = state;
+        g.cells = cells[gi];
+        long long sb = 0;
+        place_vectors(&g, h->n_pad, h0->opts.lbfgs_m, budget, &sb);
+        slot = std::max(slot, sb);
+        smem_max = std::max(smem_max, g.smem_bytes);
+        total += cells[gi];
+        state += 3LL * h->n * cells[gi];
+    }
+    if (total == 0) return 0;
+    a.n_groups = n_groups;
+    a.total_cells = total;
+    a.x = x;
+    a.v = v;
+    a.f = f;
+    a.y = y;
+    a.grad_out = grad_out;
+    a.parts = parts;
+    a.stats = stats;
+    a.work = h0->work;
+    a.p.lbfgs_m = h0->opts.lbfgs_m;
+    a.p.max_iter = h0->opts.max_iter;
+    a.p.max_halvings = h0->opts.max_halvings;
+    a.p.fixed_alpha = h0->opts.fixed_alpha;
+    a.p.tol = h0->opts.tol;
+    a.p.c1 = h0->opts.c1;
+    a.p.c2 = h0->opts.c2;
+    a.p.armijo_noise = h0->opts.armijo_noise;
+    a.p.mode = mode;
+    a.p.contraction = CONTRACT_SIMT;
+
+    const int threads = h0->threads;
+    const int smem = kFixedSmem + smem_max;
+    NPFEM_CUDA(set_cell_kernel_smem<T>(smem));
+    const int per_sm = smem > h0->smem_optin / 2 ? 1 : (smem > h0->smem_optin / 3 ? 2 : 3);
+    long long grid = std::min<long long>(total, (long long)h0->sm_count * per_sm);
+    a.slot_bytes = slot;
+    if (slot > 0) {
+        size_t need = (size_t)slot * (size_t)grid;
+        if (need > h0->scratch_bytes) {
+            if (h0->scratch) {
+                NPFEM_CUDA(cudaStreamSynchronize(stream));
+                cudaFree(h0->scratch);
+                h0->scratch = nullptr;
+                h0->scratch_bytes = 0;
+            }
+            NPFEM_CUDA(cudaMalloc(&h0->scratch, need));
+            h0->scratch_bytes = need;
+        }
+        a.scratch = h0->scratch;
+    }
+    NPFEM_CUDA(launch_cells<T>(a, (int)grid, threads, smem, stream));
+    return 0;
+}
+
+int validate_group(npfem_handle* const* meshes, int n_groups, const int32_t* cells)
+{
+    if (!meshes || n_groups < 1 || n_groups > kMaxGroups || !cells)
+        return fail(NPFEM_ERR_INVALID_ARG, "need 1..8 mesh handles and a cells_per_group array");
+    for (int g = 0; g < n_groups; ++g) {
+        if (!meshes[g]) return fail(NPFEM_ERR_INVALID_ARG, "null mesh handle");
+        if (cells[g] < 0) return fail(NPFEM_ERR_INVALID_ARG, "negative cell count");
+        if (meshes[g]->device != meshes[0]->device || meshes[g]->precision != meshes[0]->precision ||
+            meshes[g]->dt != meshes[0]->dt)
+            return fail(NPFEM_ERR_INVALID_ARG, "all handles of one call must share device, precision and dt");
+    }
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void npfem_default_opts(npfem_opts* o)
+{
+    if (!o) return;
+    o->precision = NPFEM_PREC_FP32;
+    o->lbfgs_m = 5;
+    o->max_iter = 50;
+    o->tol = 1e-6;
+    o->c1 = 1e-4;
+    o->c2 = 0.9;
+    o->max_halvings = 30;
+    o->fixed_alpha = 0;
+    o->equal_mass = 0;
+    o->armijo_noise = 4.0;
+}
+
+const char* npfem_last_error(void) { return g_last_error.c_str(); }
+
+int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_opts* opts, double dt, int device,
+                 npfem_handle** out)
+{
+    g_last_error.clear();
+    if (!mesh || !mat || !opts || !out || !mesh->tris || !mesh->rest_xyz)
+        return fail(NPFEM_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(NPFEM_ERR_INVALID_ARG, "dt must be positive");
+    if (int rc = check_opts(opts)) return rc;
+    if (mat->beta_D != 0.0)
+        return fail(NPFEM_ERR_INVALID_ARG, "beta_D != 0 (stiffness-proportional Rayleigh damping) is not supported");
+    if (!(mat->density > 0.0) || mat->kappa < 0.0 || mat->kappa > 1.0 || mat->C < 0 || mat->B < 0 || mat->D < 0 ||
+        mat->k_bend < 0 || mat->k_vol < 0 || mat->k_mat_hess < 0 || mat->alpha_D < 0)
+        return fail(NPFEM_ERR_INVALID_ARG, "material: need density > 0, kappa in [0,1], non-negative moduli");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(NPFEM_ERR_INVALID_ARG, "no such CUDA device");
+    DeviceGuard guard(device);
+
+    npfem_handle* h = new npfem_handle();
+    h->device = device;
+    h->precision = opts->precision;
+    h->dt = dt;
+    h->opts = *opts;
+    h->mat = *mat;
+    std::string err;
+    int rc = build_host_topo(mesh, mat, opts->equal_mass, &h->host, &err);
+    if (rc) {
+        delete h;
+        return fail(rc, err);
+    }
+    h->n = h->host.n;
+    h->nt = h->host.nt;
+    h->n_pad = (h->n + 3) & ~3;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+
+    auto bail = [&](int code) {
+        h->release();
+        delete h;
+        return code;
+    };
+    const int n = h->n, np = h->n_pad;
+    int e = 0;
+    // dense H~ = M~/h^2 + L in FP64, inverted on the GPU
+    std::vector<double> H((size_t)n * n, 0.0);
+    const double ms = (1.0 + dt * mat->alpha_D) / (dt * dt);
+    for (int i = 0; i < n; ++i) {
+        H[(size_t)i * n + i] += ms * h->host.mass[i];
+        for (int q = h->host.L_ptr[i]; q < h->host.L_ptr[i + 1]; ++q) H[(size_t)i * n + h->host.L_idx[q]] += h->host.L_val[q];
+    }
+    h->ainv64 = h->alloc<double>((size_t)n * n, &e);
+    double* col = h->alloc<double>(n, &e);
+    int* flag = h->alloc<int>(4, &e);
+    h->work = h->alloc<unsigned int>(4, &e);
+    if (e) return bail(e);
+    if (cudaMemcpy(h->ainv64, H.data(), H.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(flag, 0, 4 * sizeof(int)) != cudaSuccess || cudaMemset(h->work, 0, 4 * sizeof(unsigned)) != cudaSuccess)
+        return bail(fail(NPFEM_ERR_CUDA, "upload of H~ failed"));
+    cudaError_t ce = invert_spd_fp64(h->ainv64, n, col, flag, 0);
+    if (ce != cudaSuccess) return bail(fail(NPFEM_ERR_CUDA, std::string("inversion: ") + cudaGetErrorString(ce)));
+    int hflag = 0;
+    if (cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bail(fail(NPFEM_ERR_CUDA, "inversion failed"));
+    if (hflag) return bail(fail(NPFEM_ERR_NOT_SPD, "H~ is not positive definite"));
+
+    void* ainv_t = nullptr;
+    if (h->precision == NPFEM_PREC_FP64) {
+        double* a64 = h->alloc<double>((size_t)np * np, &e);
+        if (e) return bail(e);
+        ce = publish_inverse(h->ainv64, n, np, nullptr, a64, nullptr, nullptr, 0);
+        ainv_t = a64;
+    } else {
+        float* a32 = h->alloc<float>((size_t)np * np, &e);
+        if (e) return bail(e);
+        ce = publish_inverse(h->ainv64, n, np, a32, nullptr, nullptr, nullptr, 0);
+        ainv_t = a32;
+    }
+    if (ce != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return bail(fail(NPFEM_ERR_CUDA, "publishing A^-1 failed"));
+    rc = h->precision == NPFEM_PREC_FP64 ? fill_topo<double>(h, &h->td, ainv_t) : fill_topo<float>(h, &h->tf, ainv_t);
+    if (rc) return bail(rc);
+    *out = h;
+    return 0;
+}
+
+int npfem_destroy(npfem_handle* h)
+{
+    if (!h) return fail(NPFEM_ERR_INVALID_ARG, "null handle");
+    {
+        DeviceGuard guard(h->device);
+        cudaDeviceSynchronize();
+        h->release();
+    }
+    delete h;
+    return 0;
+}
+
+int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
+               const void* f_ext, double dt, void* stream, npfem_cell_stats* stats)
+{
+    if (int rc = validate_group(meshes, n_groups, cells_per_group)) return rc;
+    if (!x || !v || !f_ext) return fail(NPFEM_ERR_INVALID_ARG, "null state pointer");
+    if (dt != meshes[0]->dt) return fail(NPFEM_ERR_INVALID_ARG, "dt differs from the handle's dt");
+    DeviceGuard guard(meshes[0]->device);
+    std::lock_guard<std::mutex> lk(meshes[0]->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (meshes[0]->precision == NPFEM_PREC_FP64)
+        return run_cells<double>(meshes, n_groups, cells_per_group, (double*)x, (double*)v, (const double*)f_ext,
+                                 nullptr, nullptr, nullptr, stats, 0, s);
+    return run_cells<float>(meshes, n_groups, cells_per_group, (float*)x, (float*)v, (const float*)f_ext, nullptr,
+                            nullptr, nullptr, stats, 0, s);
+}
+
+int npfem_step_host(npfem_handle* h, int n_cells, void* x_host, void* v_host, const void* f_host, double dt,
+                    void* stream, npfem_cell_stats* stats_host)
+{
+    if (!h || n_cells < 0 || !x_host || !v_host || !f_host) return fail(NPFEM_ERR_INVALID_ARG, "null argument");
+    if (dt != h->dt) return fail(NPFEM_ERR_INVALID_ARG, "dt differs from the handle's dt");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t es = h->precision == NPFEM_PREC_FP64 ? 8 : 4;
+    const size_t bytes = (size_t)n_cells * 3 * h->n * es;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        if ((size_t)n_cells > h->host_cells) {
+            NPFEM_CUDA(cudaStreamSynchronize(s));
+            if (h->hx) cudaFree(h->hx);
+            if (h->hv) cudaFree(h->hv);
+            if (h->hf) cudaFree(h->hf);
+            if (h->hstats) cudaFree(h->hstats);
+            h->hx = h->hv = h->hf = nullptr;
+            h->hstats = nullptr;
+            h->host_cells = 0;
+            NPFEM_CUDA(cudaMalloc(&h->hx, bytes));
+            NPFEM_CUDA(cudaMalloc(&h->hv, bytes));
+            NPFEM_CUDA(cudaMalloc(&h->hf, bytes));
+            NPFEM_CUDA(cudaMalloc(&h->hstats, sizeof(npfem_cell_stats) * (size_t)std::max(n_cells, 1)));
+            h->host_cells = (size_t)n_cells;
+        }
+    }
+    if (n_cells == 0) return 0;
+    NPFEM_CUDA(cudaMemcpyAsync(h->hx, x_host, bytes, cudaMemcpyHostToDevice, s));
+    NPFEM_CUDA(cudaMemcpyAsync(h->hv, v_host, bytes, cudaMemcpyHostToDevice, s));
+    NPFEM_CUDA(cudaMemcpyAsync(h->hf, f_host, bytes, cudaMemcpyHostToDevice, s));
+    int32_t cells = n_cells;
+    npfem_handle* hs[1] = {h};
+    int rc = npfem_step(hs, 1, &cells, h->hx, h->hv, h->hf, dt, stream, stats_host ? h->hstats : nullptr);
+    if (rc) return rc;
+    NPFEM_CUDA(cudaMemcpyAsync(x_host, h->hx, bytes, cudaMemcpyDeviceToHost, s));
+    NPFEM_CUDA(cudaMemcpyAsync(v_host, h->hv, bytes, cudaMemcpyDeviceToHost, s));
+    if (stats_host)
+        NPFEM_CUDA(cudaMemcpyAsync(stats_host, h->hstats, sizeof(npfem_cell_stats) * n_cells, cudaMemcpyDeviceToHost, s));
+    NPFEM_CUDA(cudaStreamSynchronize(s));
+    return 0;
+}
+
+int npfem_eval(npfem_handle* h, int n_cells, const void* x, const void* y, void* grad, double* parts, void* stream)
+{
+    if (!h || n_cells < 0 || !x || !y || !grad || !parts) return fail(NPFEM_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(h->device);
+    std::lock_guard<std::mutex> lk(h->mu);
+    npfem_handle* hs[1] = {h};
+    int32_t cells = n_cells;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (h->precision == NPFEM_PREC_FP64)
+        return run_cells<double>(hs, 1, &cells, (double*)x, nullptr, nullptr, (const double*)y, (double*)grad, parts,
+                                 nullptr, 1, s);
+    return run_cells<float>(hs, 1, &cells, (float*)x, nullptr, nullptr, (const float*)y, (float*)grad, parts, nullptr,
+                            1, s);
+}
+
+int npfem_get_inverse(npfem_handle* h, double* out_host)
+{
+    if (!h || !out_host) return fail(NPFEM_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(h->device);
+    NPFEM_CUDA(cudaMemcpy(out_host, h->ainv64, sizeof(double) * (size_t)h->n * h->n, cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+int npfem_get_rest_info(npfem_handle* h, double* masses_host, double* scalars_host)
+{
+    if (!h) return fail(NPFEM_ERR_INVALID_ARG, "null handle");
+    if (masses_host) memcpy(masses_host, h->host.mass.data(), sizeof(double) * h->n);
+    if (scalars_host) {
+        scalars_host[0] = h->host.V0;
+        scalars_host[1] = h->host.A0;
+        scalars_host[2] = h->host.lbar;
+        scalars_host[3] = h->host.mtotal;
+    }
+    return 0;
+}
+
+}  // extern "C"

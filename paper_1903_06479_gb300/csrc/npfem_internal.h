@@ -1,0 +1,119 @@
+// Internal declarations shared by the translation units of libnpfem.so.
+// Not part of the public ABI (see include/npfem.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/npfem.h"
+
+namespace npfem {
+
+constexpr int kMaxGroups = 8;     // meshes per npfem_step launch
+constexpr int kMaxHistory = 8;    // L-BFGS window limit
+constexpr int kNumBaseVecs = 8;   // XN U UT G GT GC UY D, then S[m], Y[m]
+constexpr int kMaxVecs = kNumBaseVecs + 2 * kMaxHistory;
+constexpr int kFixedSmem = 6144;  // reduction scratch + per-cell scalars at the start of dynamic smem
+
+enum Vec { V_XN = 0, V_U = 1, V_UT = 2, V_G = 3, V_GT = 4, V_GC = 5, V_UY = 6, V_D = 7, V_SBASE = 8 };
+
+enum Contraction { CONTRACT_SIMT = 0, CONTRACT_TC_TF32 = 1, CONTRACT_TC_BF16 = 2 };
+
+// Device-side tables of one mesh topology (all pointers are device memory owned by
+// the handle).  T is the solver's scalar type (float or double).
+template <typename T>
+struct TopoDev {
+    int n, nt, n_pad, nnz;
+    const ushort4* tri;          // [nt] vertex indices (i, j, k, 0)
+    const T* dminv;              // [nt][4] row-major D_m^{-1}
+    const T* W;                  // [nt] rest triangle areas
+    const T* mass;               // [n] lumped masses
+    const T* inv_mass;           // [n]
+    const T* bend_w;             // [n] k_bend * mixed Voronoi area
+    const T* dg_norm;            // [n] |delta_g| of the rest shape
+    const T* csum;               // [n] sum_j c_ij
+    const T* nsign;              // [n] +-1: orientation of delta_g against the rest normal
+    const int* ring_ptr;         // [n + 1]
+    const unsigned short* ring_idx;  // [nnz]
+    const T* ring_c;             // [nnz] cotangent weights / (2 A_i)
+    const T* ainv;               // [n_pad][n_pad] A^-1 in T (zero padding)
+    const void* ainv_lp;         // A^-1 for the tensor-core contraction (bf16 or tf32-rounded fp32)
+    const int* h_ptr;            // sparse H~ (CSR, fp32) for the refinement sweep
+    const unsigned short* h_idx;
+    const float* h_val;
+    T C, B, Dsk, kvol;           // material
+    T h, inv_h2, inertia_scale;  // time step; inertia_scale = 1 + h alpha_D
+    T kappa, lbar, inv_lbar;
+    double V0;
+};
+
+// One mesh topology inside one launch.
+template <typename T>
+struct GroupDesc {
+    TopoDev<T> topo;
+    long long cell_begin;  // first global work item of the group
+    long long state_off;   // element offset of the group's first cell in x / v / f
+    int cells;
+    int smem_bytes;        // dynamic smem this group needs (after kFixedSmem)
+    int loc[kMaxVecs];     // >= 0: byte offset in smem; < 0: -(byte offset in the CTA's global slot) - 1
+};
+
+struct SolverParams {
+    int lbfgs_m, max_iter, max_halvings, fixed_alpha;
+    double tol, c1, c2, armijo_noise;
+    int mode;         // 0 = time step, 1 = objective/gradient evaluation only
+    int contraction;  // Contraction
+};
+
+template <typename T>
+struct LaunchArgs {
+    GroupDesc<T> g[kMaxGroups];
+    int n_groups;
+    long long total_cells;
+    T* x;
+    T* v;
+    const T* f;
+    const T* y;        // eval mode: inertia target
+    T* grad_out;       // eval mode
+    double* parts;     // eval mode: 8 doubles per cell
+    npfem_cell_stats* stats;
+    char* scratch;     // per-CTA global slots for vectors that do not fit in smem
+    long long slot_bytes;
+    unsigned int* work;  // [0] next work item, [1] finished CTAs (reset by the last CTA)
+    SolverParams p;
+};
+
+// ---- host-side rest precompute (npfem_setup.cpp) ------------------------------
+struct HostTopo {
+    int n = 0, nt = 0;
+    std::vector<int> tri;                     // [nt][3]
+    std::vector<double> dminv, W;             // [nt][4], [nt]
+    std::vector<double> mass, avor, bend_w, dg_norm, csum, nsign;  // [n]
+    std::vector<int> ring_ptr, ring_idx;      // CSR one-ring
+    std::vector<double> ring_c;
+    std::vector<int> L_ptr, L_idx;            // CSR of L (full symmetric)
+    std::vector<double> L_val;
+    double V0 = 0, A0 = 0, lbar = 0, mtotal = 0;
+};
+
+// Returns 0 or a negative NPFEM_ERR code with a message in *err.
+int build_host_topo(const npfem_mesh* mesh, const npfem_material* mat, int equal_mass, HostTopo* out,
+                    std::string* err);
+
+// ---- kernels (npfem_factor.cu, npfem_solver.cu) ---------------------------------
+// In-place FP64 Gauss-Jordan inversion of an SPD n x n matrix on the GPU; sets
+// *not_spd when a pivot is not positive.
+cudaError_t invert_spd_fp64(double* A, int n, double* col_scratch, int* d_flag, cudaStream_t s);
+// Symmetrise A^-1 (FP64, n x n) and write padded copies in fp32 / fp64 / bf16.
+cudaError_t publish_inverse(const double* A, int n, int n_pad, float* out32, double* out64, void* out_bf16,
+                            float* out_tf32, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s);
+template <typename T>
+cudaError_t set_cell_kernel_smem(int bytes);
+
+}  // namespace npfem

@@ -1,0 +1,719 @@
+// npFEM time step on the GPU: one thread block solves one red-blood-cell membrane at
+// a time (persistent blocks pull cells from a work counter), with every per-cell
+// vector of the quasi-Newton solve resident in shared memory when it fits.
+//
+// Per cell (Algorithm 1 of arXiv:1903.06479):
+//   y = x_n + h M~^{-1} M v_n + h^2 M~^{-1} F_ext             (first guess)
+//   repeat: residual test; d = -LBFGS(H~^{-1}) grad g; alpha = 1, 1/2, ...
+//           x + alpha d -> projections, energies, g, grad g   (line search)
+//   v_{n+1} = (x_{n+1} - x_n)/h; post-convergence dissipation (Sec. 2.1.4)
+//
+// The solve runs on the increment u = x - x_n in cell-local coordinates (origin at
+// the cell's first vertex) so that FP32 keeps the small per-step displacements:
+// edges are (X_j - X_i) + (u_j - u_i) and the enclosed volume is V(x_n) + dV(u).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "npfem_internal.h"
+
+namespace npfem {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+struct Unit;
+template <>
+struct Unit<float> {
+    static constexpr double u = 5.9604644775390625e-08;
+    static constexpr float sl2_rel = 2.0e-7f;
+    static constexpr float tiny = 1.0e-37f;
+};
+template <>
+struct Unit<double> {
+    static constexpr double u = 1.1102230246251565e-16;
+    static constexpr double sl2_rel = 4.0e-16;
+    static constexpr double tiny = 1.0e-300;
+};
+
+// Block-wide sum of K doubles; every thread receives the totals in the same order.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* red)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[w * K + k] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int q = 0; q < nw; ++q) s += red[q * K + k];
+        v[k] = s;
+    }
+    __syncthreads();
+}
+
+// SL(2) projection of the principal stretches (Sec. 2.1.2, area preservation):
+// Sigma* = diag(a, 1/a) closest to diag(s1, s2), s1 >= s2.  With a = 1 + t,
+// s1 = 1 + e1, s2 = 1 + e2 the stationarity condition a^4 - s1 a^3 + s2 a - 1 = 0
+// reads phi(t) = (t - e1)(1 + t)^3 + t (1 + e2) + e2 = 0.  The minimiser is the
+// largest root, the only one in [max(0, (e1 - 1)/2), 1 + e1], where phi is convex
+// and changes sign; safeguarded Newton from the small-strain root (e1 - e2)/2.
+template <typename T>
+__device__ __forceinline__ T sl2_t(T e1, T e2)
+{
+    T lo = e1 > T(1) ? T(0.5) * (e1 - T(1)) : T(0);
+    T hi = T(1) + e1;
+    T t = T(0.5) * (e1 - e2);
+    t = t < lo ? lo : (t > hi ? hi : t);
+    for (int it = 0; it < 60; ++it) {
+        T a1 = T(1) + t;
+        T a2 = a1 * a1;
+        T tm = t - e1;
+        T ph = tm * a2 * a1 + t * (T(1) + e2) + e2;
+        if (ph == T(0)) break;
+        if (ph < T(0)) lo = t; else hi = t;
+        T dph = a2 * a1 + T(3) * tm * a2 + (T(1) + e2);
+        T tn = t - ph / dph;
+        if (!(tn > lo && tn < hi)) tn = T(0.5) * (lo + hi);
+        T step = tn - t;
+        t = tn;
+        if (fabs(step) <= Unit<T>::sl2_rel * (fabs(t) + fabs(e1) + fabs(e2)) + Unit<T>::tiny || hi - lo <= T(0)) break;
+    }
+    return t;
+}
+
+template <typename T>
+struct EvalOut {
+    double E, Earea, Esk, Ebend, Evol, Ein, V, res, noise;
+    bool bad;
+};
+
+template <typename T>
+__device__ __forceinline__ T* vec_ptr(const GroupDesc<T>& gd, unsigned char* smem, char* slot, int v)
+{
+    int l = gd.loc[v];
+    return l >= 0 ? reinterpret_cast<T*>(smem + kFixedSmem + l) : reinterpret_cast<T*>(slot + (-(long long)l - 1));
+}
+
+// Volume of the cell at x_n in local coordinates: V = sum_t X_i . (E1 x E2) / 6.
+template <typename T>
+__device__ double volume_at_xn(const TopoDev<T>& tp, const T* XN, double* red)
+{
+    const int np = tp.n_pad;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < tp.nt; t += blockDim.x) {
+        ushort4 tv = __ldg(&tp.tri[t]);
+        T Xi[3], E1[3], E2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Xi[c] = XN[c * np + tv.x];
+            E1[c] = XN[c * np + tv.y] - Xi[c];
+            E2[c] = XN[c * np + tv.z] - Xi[c];
+        }
+        T cx = E1[1] * E2[2] - E1[2] * E2[1], cy = E1[2] * E2[0] - E1[0] * E2[2], cz = E1[0] * E2[1] - E1[1] * E2[0];
+        acc += (double)(Xi[0] * cx + Xi[1] * cy + Xi[2] * cz);
+    }
+    double v[1] = {acc};
+    block_sum<1>(v, red);
+    return v[0] / 6.0;
+}
+
+// Objective g and gradient at x_n + U (Eq. GeneralizedObjectiveFunction and its
+// derivative): inertia, local area preservation and bending (projective dynamics
+// gradients), global volume conservation (PD gradient with the linearised
+// projection), modified Skalak (first Piola-Kirchhoff forces).
+template <typename T>
+__device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T* UY, T* Gout, T* GC,
+                               double Vn, double* red)
+{
+    const int n = tp.n, np = tp.n_pad, N3 = 3 * np, tid = threadIdx.x, NT = blockDim.x;
+    for (int e = tid; e < N3; e += NT) {
+        Gout[e] = T(0);
+        GC[e] = T(0);
+    }
+    __syncthreads();
+
+    const T Cs = tp.C, Bs = tp.B, Ds = tp.Dsk;
+    const T sixth = T(1) / T(6);
+    double eA = 0.0, eS = 0.0, dV = 0.0, noise = 0.0;
+    int bad = 0;
+    for (int t = tid; t < tp.nt; t += NT) {
+        const ushort4 tv = __ldg(&tp.tri[t]);
+        const int i = tv.x, j = tv.y, k = tv.z;
+        T Di0, Di1, Di2, Di3;
+        if constexpr (sizeof(T) == 4) {
+            float4 d4 = __ldg(reinterpret_cast<const float4*>(tp.dminv) + t);
+            Di0 = d4.x; Di1 = d4.y; Di2 = d4.z; Di3 = d4.w;
+        } else {
+            double2 a2 = __ldg(reinterpret_cast<const double2*>(tp.dminv) + 2 * t);
+            double2 b2 = __ldg(reinterpret_cast<const double2*>(tp.dminv) + 2 * t + 1);
+            Di0 = a2.x; Di1 = a2.y; Di2 = b2.x; Di3 = b2.y;
+        }
+        const T Wt = __ldg(&tp.W[t]);
+        T Xi[3], E1[3], E2[3], Ui[3], d1[3], d2[3], e1[3], e2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Xi[c] = XN[c * np + i];
+            E1[c] = XN[c * np + j] - Xi[c];
+            E2[c] = XN[c * np + k] - Xi[c];
+            Ui[c] = U[c * np + i];
+            d1[c] = U[c * np + j] - Ui[c];
+            d2[c] = U[c * np + k] - Ui[c];
+            e1[c] = E1[c] + d1[c];
+            e2[c] = E2[c] + d2[c];
+        }
+        // F = D_s D_m^{-1} (3 x 2), columns F0, F1
+        T F0[3], F1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            F0[c] = e1[c] * Di0 + e2[c] * Di2;
+            F1[c] = e1[c] * Di1 + e2[c] * Di3;
+        }
+        const T aa = F0[0] * F0[0] + F0[1] * F0[1] + F0[2] * F0[2];
+        const T bb = F0[0] * F1[0] + F0[1] * F1[1] + F0[2] * F1[2];
+        const T cc = F1[0] * F1[0] + F1[1] * F1[1] + F1[2] * F1[2];
+        // principal stretches from the eigenvalues of C = F^T F, kept as s - 1
+        const T meanm1 = T(0.5) * ((aa - T(1)) + (cc - T(1)));
+        const T dif = T(0.5) * (aa - cc);
+        const T rad = sqrt(dif * dif + bb * bb);
+        const T m1 = meanm1 + rad, m2 = meanm1 - rad;
+        const T s1 = sqrt(T(1) + m1);
+        const T q2 = T(1) + m2;
+        const T s2 = q2 > T(0) ? sqrt(q2) : T(0);
+        if (!(s2 > T(1e-6) * s1) || !(s1 < T(1e30))) {
+            bad = 1;
+            continue;
+        }
+        const T e1s = m1 / (s1 + T(1)), e2s = m2 / (s2 + T(1));
+        // area preservation: distance to SL(2)
+        const T tsl = sl2_t(e1s, e2s);
+        const T dd1 = e1s - tsl, dd2 = e2s + tsl / (T(1) + tsl);
+        // modified Skalak, f(s) = B/8 (s^2 - 1)^2 + D/4 (s - 1)^4, written in e = s - 1
+        const T f1 = T(0.125) * Bs * (e1s * (T(2) + e1s)) * (e1s * (T(2) + e1s)) + T(0.25) * Ds * e1s * e1s * e1s * e1s;
+        const T f2 = T(0.125) * Bs * (e2s * (T(2) + e2s)) * (e2s * (T(2) + e2s)) + T(0.25) * Ds * e2s * e2s * e2s * e2s;
+        const T fp1 = T(0.5) * Bs * (T(1) + e1s) * e1s * (T(2) + e1s) + Ds * e1s * e1s * e1s;
+        const T fp2 = T(0.5) * Bs * (T(1) + e2s) * e2s * (T(2) + e2s) + Ds * e2s * e2s * e2s;
+        eA += (double)(T(0.5) * Cs * Wt * (dd1 * dd1 + dd2 * dd2));
+        eS += (double)(Wt * (f1 + f2));
+        // dE/dF = F V diag(k) V^T with k_a = W (C (s_a - s*_a) + f'(s_a)) / s_a
+        const T k1 = Wt * (Cs * dd1 + fp1) / s1;
+        const T k2 = Wt * (Cs * dd2 + fp2) / s2;
+        noise += (double)(fabs(k1) * s1 * s1 + fabs(k2) * s2 * s2);
+        T vx, vy;
+        if (rad == T(0)) {
+            vx = T(1); vy = T(0);
+        } else if (dif >= T(0)) {
+            vx = dif + rad; vy = bb;
+        } else {
+            vx = bb; vy = rad - dif;
+        }
+        const T inv = T(1) / sqrt(vx * vx + vy * vy);
+        vx *= inv;
+        vy *= inv;
+        const T K00 = k1 * vx * vx + k2 * vy * vy;
+        const T K11 = k1 * vy * vy + k2 * vx * vx;
+        const T K01 = (k1 - k2) * vx * vy;
+        T cr[3], dcr[3];
+        cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        // cross-product change relative to x_n: E1 x d2 + d1 x E2 + d1 x d2
+        dcr[0] = (E1[1] * d2[2] - E1[2] * d2[1]) + (d1[1] * E2[2] - d1[2] * E2[1]) + (d1[1] * d2[2] - d1[2] * d2[1]);
+        dcr[1] = (E1[2] * d2[0] - E1[0] * d2[2]) + (d1[2] * E2[0] - d1[0] * E2[2]) + (d1[2] * d2[0] - d1[0] * d2[2]);
+        dcr[2] = (E1[0] * d2[1] - E1[1] * d2[0]) + (d1[0] * E2[1] - d1[1] * E2[0]) + (d1[0] * d2[1] - d1[1] * d2[0]);
+        dV += (double)((Xi[0] * dcr[0] + Xi[1] * dcr[1] + Xi[2] * dcr[2]) + (Ui[0] * cr[0] + Ui[1] * cr[1] + Ui[2] * cr[2]));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T G0 = F0[c] * K00 + F1[c] * K01;
+            const T G1 = F0[c] * K01 + F1[c] * K11;
+            const T gj = G0 * Di0 + G1 * Di1;
+            const T gk = G0 * Di2 + G1 * Di3;
+            atomicAdd(&Gout[c * np + j], gj);
+            atomicAdd(&Gout[c * np + k], gk);
+            atomicAdd(&Gout[c * np + i], -(gj + gk));
+            const T g6 = cr[c] * sixth;
+            atomicAdd(&GC[c * np + i], g6);
+            atomicAdd(&GC[c * np + j], g6);
+            atomicAdd(&GC[c * np + k], g6);
+        }
+    }
+    __syncthreads();
+
+    // bending per vertex (Eq. BendingDiscretizedPotential) and |grad C|^2
+    double eB = 0.0, gc2 = 0.0;
+    for (int i = tid; i < n; i += NT) {
+        const int b = __ldg(&tp.ring_ptr[i]), e = __ldg(&tp.ring_ptr[i + 1]);
+        T dfn[3] = {T(0), T(0), T(0)}, dfu[3] = {T(0), T(0), T(0)};
+        T Xi[3], Ui[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Xi[c] = XN[c * np + i];
+            Ui[c] = U[c * np + i];
+        }
+        for (int q = b; q < e; ++q) {
+            const int jn = __ldg(&tp.ring_idx[q]);
+            const T cq = __ldg(&tp.ring_c[q]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dfn[c] += cq * (XN[c * np + jn] - Xi[c]);
+                dfu[c] += cq * (U[c * np + jn] - Ui[c]);
+            }
+        }
+        T df[3] = {dfn[0] + dfu[0], dfn[1] + dfu[1], dfn[2] + dfu[2]};
+        const T nf = sqrt(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+        const T ng = __ldg(&tp.dg_norm[i]);
+        T r[3];
+        if (ng > T(0) && nf > T(1e-12) * ng) {
+            const T sc = (nf - ng) / nf;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[c] = df[c] * sc;
+        } else if (ng > T(0)) {
+            // delta_f ~ 0: the rotation is free; take the current vertex normal
+            T gcv[3] = {GC[i], GC[np + i], GC[2 * np + i]};
+            const T gn = sqrt(gcv[0] * gcv[0] + gcv[1] * gcv[1] + gcv[2] * gcv[2]);
+            const T s = gn > T(0) ? __ldg(&tp.nsign[i]) * ng / gn : T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[c] = df[c] - s * gcv[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[c] = df[c];
+        }
+        const T w = __ldg(&tp.bend_w[i]);
+        const T rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        eB += (double)(T(0.5) * w * rr);
+        noise += (double)(w * sqrt(rr) * nf);
+        for (int q = b; q < e; ++q) {
+            const int jn = __ldg(&tp.ring_idx[q]);
+            const T wc = w * __ldg(&tp.ring_c[q]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(&Gout[c * np + jn], wc * r[c]);
+        }
+        const T wcs = w * __ldg(&tp.csum[i]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) atomicAdd(&Gout[c * np + i], -wcs * r[c]);
+        gc2 += (double)(GC[i] * GC[i] + GC[np + i] * GC[np + i] + GC[2 * np + i] * GC[2 * np + i]);
+    }
+    double s7[7] = {eA, eS, eB, dV, gc2, noise, (double)bad};
+    block_sum<7>(s7, red);
+
+    EvalOut<T> o;
+    o.Earea = s7[0];
+    o.Esk = s7[1];
+    o.Ebend = s7[2];
+    o.V = Vn + s7[3] / 6.0;
+    const double Cv = o.V - tp.V0;
+    o.Evol = 0.5 * (double)tp.kvol * Cv * Cv / s7[4];
+    o.bad = s7[6] != 0.0;
+    const T volc = (T)((double)tp.kvol * Cv / s7[4]);
+
+    // inertia (M~ = (1 + h alpha_D) M, diagonal), volume gradient, residual
+    const T ms = tp.inertia_scale * tp.inv_h2, h2 = tp.h * tp.h;
+    double eI = 0.0, res2 = 0.0;
+    for (int i = tid; i < n; i += NT) {
+        const T m = __ldg(&tp.mass[i]);
+        const T hm = h2 * __ldg(&tp.inv_mass[i]);
+        T g2 = T(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T du = U[c * np + i] - UY[c * np + i];
+            const T gv = Gout[c * np + i] + volc * GC[c * np + i] + m * ms * du;
+            Gout[c * np + i] = gv;
+            eI += (double)(T(0.5) * m * ms * du * du);
+            g2 += gv * gv;
+        }
+        res2 += (double)(hm * hm * g2);
+    }
+    double s2[2] = {eI, res2};
+    block_sum<2>(s2, red);
+    o.Ein = s2[0];
+    o.E = o.Ein + o.Earea + o.Esk + o.Ebend + o.Evol;
+    o.res = sqrt(s2[1] / (double)n) * (double)tp.inv_lbar;
+    o.noise = 4.0 * Unit<T>::u * (s7[5] + 2.0 * o.Ein);
+    return o;
+}
+
+// R = A^-1 Q for the three coordinate rows (A symmetric: column access is
+// coalesced across the lanes of a warp, Q is broadcast from shared memory).
+template <typename T>
+__device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R)
+{
+    const int n = tp.n, np = tp.n_pad, N3 = 3 * np;
+    for (int e = threadIdx.x; e < N3; e += blockDim.x) R[e] = T(0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ntile = (n + 31) >> 5;
+    int nsplit = 1;
+    for (int s = 1; s <= 8; ++s) {
+        int items = ntile * s, rounds = (items + nw - 1) / nw;
+        if (items * 10 >= rounds * nw * 9) { nsplit = s; break; }
+        nsplit = s;
+    }
+    const int chunk = (n + nsplit - 1) / nsplit;
+    const T* __restrict__ A = tp.ainv;
+    for (int item = warp; item < ntile * nsplit; item += nw) {
+        const int rt = item / nsplit, js = item - rt * nsplit;
+        const int row = rt * 32 + lane;
+        const int j0 = js * chunk, j1 = min(n, j0 + chunk);
+        T a0 = T(0), a1 = T(0), a2 = T(0);
+        if (row < n) {
+            int j = j0;
+            for (; j + 4 <= j1; j += 4) {
+                T av[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) av[u] = __ldg(&A[(size_t)(j + u) * np + row]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a0 += av[u] * Q[j + u];
+                    a1 += av[u] * Q[np + j + u];
+                    a2 += av[u] * Q[2 * np + j + u];
+                }
+            }
+            for (; j < j1; ++j) {
+                const T av = __ldg(&A[(size_t)j * np + row]);
+                a0 += av * Q[j];
+                a1 += av * Q[np + j];
+                a2 += av * Q[2 * np + j];
+            }
+            atomicAdd(&R[row], a0);
+            atomicAdd(&R[np + row], a1);
+            atomicAdd(&R[2 * np + row], a2);
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long long cell, long long item,
+                           unsigned char* smem)
+{
+    const TopoDev<T>& tp = gd.topo;
+    const int n = tp.n, np = tp.n_pad, N3 = 3 * np, tid = threadIdx.x, NT = blockDim.x;
+    double* red = reinterpret_cast<double*>(smem);            // 32 warps x 16 doubles
+    double* s_rho = reinterpret_cast<double*>(smem + 4096);   // [kMaxHistory]
+    double* s_alpha = s_rho + kMaxHistory;                    // [kMaxHistory]
+    char* slot = a.scratch ? a.scratch + (long long)blockIdx.x * a.slot_bytes : nullptr;
+
+    T* XN = vec_ptr(gd, smem, slot, V_XN);
+    T* u = vec_ptr(gd, smem, slot, V_U);
+    T* ut = vec_ptr(gd, smem, slot, V_UT);
+    T* g = vec_ptr(gd, smem, slot, V_G);
+    T* gt = vec_ptr(gd, smem, slot, V_GT);
+    T* GCv = vec_ptr(gd, smem, slot, V_GC);
+    T* UYv = vec_ptr(gd, smem, slot, V_UY);
+    T* Dv = vec_ptr(gd, smem, slot, V_D);
+    const int M = a.p.lbfgs_m;
+
+    const long long so = gd.state_off + cell * 3LL * n;
+    const T h = tp.h;
+    const T inv_ms = T(1) / tp.inertia_scale;
+    const bool eval_mode = a.p.mode == 1;
+
+    // ---- load the cell: local coordinates around vertex 0, first guess
+    {
+        const T* x = a.x + so;
+        const T o0 = x[0], o1 = x[n], o2 = x[2 * n];
+        for (int e = tid; e < N3; e += NT) {
+            const int c = e / np, i = e - c * np;
+            T xn = T(0), uy = T(0);
+            if (i < n) {
+                const T xv = x[c * n + i];
+                xn = xv - (c == 0 ? o0 : (c == 1 ? o1 : o2));
+                if (eval_mode) {
+                    uy = a.y[so + c * n + i] - xv;
+                } else {
+                    const T vv = a.v[so + c * n + i], fv = a.f[so + c * n + i];
+                    uy = (h * vv + h * h * fv * __ldg(&tp.inv_mass[i])) * inv_ms;
+                }
+            }
+            XN[e] = xn;
+            UYv[e] = uy;
+            u[e] = eval_mode ? T(0) : uy;
+        }
+    }
+    __syncthreads();
+    const double Vn = volume_at_xn(tp, XN, red);
+
+    EvalOut<T> ev = evaluate(tp, XN, u, UYv, g, GCv, Vn, red);
+    int evals = 1, iters = 0, status = NPFEM_CELL_OK;
+
+    if (eval_mode) {
+        for (int e = tid; e < 3 * n; e += NT) {
+            const int c = e / n, i = e - c * n;
+            a.grad_out[so + e] = g[c * np + i];
+        }
+        if (tid == 0) {
+            double* P = a.parts + 8 * item;
+            P[0] = ev.Ein; P[1] = ev.Earea; P[2] = ev.Esk; P[3] = ev.Ebend; P[4] = ev.Evol;
+            P[5] = ev.V; P[6] = ev.E; P[7] = ev.res;
+        }
+        __syncthreads();
+        return;
+    }
+
+    // ---- quasi-Newton iterations (L-BFGS, Nocedal & Wright Algorithm 7.4, H0 = H~^-1)
+    int head = 0, count = 0;
+    double E = ev.E, noiseE = ev.noise, res = ev.res;
+    bool nonfinite = ev.bad || !isfinite(ev.E) || !isfinite(ev.res);
+    while (!nonfinite) {
+        if (res <= a.p.tol) break;
+        if (iters >= a.p.max_iter) { status = NPFEM_CELL_MAXITER; break; }
+
+        // first loop: q = g; alpha_i = rho_i s_i^T q; q -= alpha_i y_i (newest first)
+        for (int e = tid; e < N3; e += NT) Dv[e] = g[e];
+        __syncthreads();
+        for (int q = 0; q < count; ++q) {
+            const int i = (head - 1 - q + M) % M;
+            const T* S = vec_ptr(gd, smem, slot, V_SBASE + i);
+            const T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + i);
+            double d1[1] = {0.0};
+            T acc = T(0);
+            for (int e = tid; e < N3; e += NT) acc += S[e] * Dv[e];
+            d1[0] = (double)acc;
+            block_sum<1>(d1, red);
+            const double al = s_rho[i] * d1[0];
+            if (tid == 0) s_alpha[i] = al;
+            for (int e = tid; e < N3; e += NT) Dv[e] -= (T)al * Y[e];
+            __syncthreads();
+        }
+        // r = H0 q through the dense inverse
+        contract_simt(tp, Dv, GCv);
+        // second loop: beta = rho_i y_i^T r; r += s_i (alpha_i - beta) (oldest first)
+        for (int q = count - 1; q >= 0; --q) {
+            const int i = (head - 1 - q + M) % M;
+            const T* S = vec_ptr(gd, smem, slot, V_SBASE + i);
+            const T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + i);
+            T acc = T(0);
+            for (int e = tid; e < N3; e += NT) acc += Y[e] * GCv[e];
+            double d1[1] = {(double)acc};
+            block_sum<1>(d1, red);
+            const double be = s_rho[i] * d1[0];
+            const T coef = (T)(s_alpha[i] - be);
+            for (int e = tid; e < N3; e += NT) GCv[e] += S[e] * coef;
+            __syncthreads();
+        }
+        double gd1[1];
+        {
+            T acc = T(0);
+            for (int e = tid; e < N3; e += NT) {
+                const T dv = -GCv[e];
+                Dv[e] = dv;
+                acc += g[e] * dv;
+            }
+            gd1[0] = (double)acc;
+            block_sum<1>(gd1, red);
+        }
+        double gdv = gd1[0];
+        if (!(gdv < 0.0)) {
+            // not a descent direction: drop the history, d = -H~^-1 g
+            count = 0;
+            contract_simt(tp, g, GCv);
+            T acc = T(0);
+            for (int e = tid; e < N3; e += NT) {
+                const T dv = -GCv[e];
+                Dv[e] = dv;
+                acc += g[e] * dv;
+            }
+            double t1[1] = {(double)acc};
+            block_sum<1>(t1, red);
+            gdv = t1[0];
+        }
+
+        // backtracking line search alpha = 1, 1/2, ... (Armijo)
+        double alpha = 1.0;
+        bool accepted = false;
+        EvalOut<T> et;
+        for (int hv = 0; hv <= a.p.max_halvings; ++hv) {
+            const T al = (T)alpha;
+            for (int e = tid; e < N3; e += NT) ut[e] = u[e] + al * Dv[e];
+            __syncthreads();
+            et = evaluate(tp, XN, ut, UYv, gt, GCv, Vn, red);
+            ++evals;
+            if (a.p.fixed_alpha ||
+                (!et.bad && et.E <= E + a.p.c1 * alpha * gdv + a.p.armijo_noise * (et.noise + noiseE))) {
+                accepted = true;
+                break;
+            }
+            alpha *= 0.5;
+        }
+        if (!accepted) {
+            status = NPFEM_CELL_LINESEARCH_FAIL;
+            break;
+        }
+        // history pair (s, y) = (x_{k+1} - x_k, grad_{k+1} - grad_k), kept when the
+        // curvature condition holds and s^T y > 0
+        if (M > 0) {
+            T sy = T(0), ss = T(0), yy = T(0), gtd = T(0);
+            for (int e = tid; e < N3; e += NT) {
+                const T se = ut[e] - u[e], ye = gt[e] - g[e];
+                sy += se * ye;
+                ss += se * se;
+                yy += ye * ye;
+                gtd += gt[e] * Dv[e];
+            }
+            double s4[4] = {(double)sy, (double)ss, (double)yy, (double)gtd};
+            block_sum<4>(s4, red);
+            if (s4[3] >= a.p.c2 * gdv && s4[0] > 1e-12 * sqrt(s4[1] * s4[2])) {
+                T* S = vec_ptr(gd, smem, slot, V_SBASE + head);
+                T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + head);
+                for (int e = tid; e < N3; e += NT) {
+                    S[e] = ut[e] - u[e];
+                    Y[e] = gt[e] - g[e];
+                }
+                if (tid == 0) s_rho[head] = 1.0 / s4[0];
+                head = (head + 1) % M;
+                count = count < M ? count + 1 : M;
+                __syncthreads();
+            }
+        }
+        T* tp1 = u; u = ut; ut = tp1;
+        T* tp2 = g; g = gt; gt = tp2;
+        E = et.E;
+        noiseE = et.noise;
+        res = et.res;
+        ev = et;
+        ++iters;
+        nonfinite = et.bad || !isfinite(et.E) || !isfinite(et.res);
+    }
+    if (nonfinite) status = NPFEM_CELL_NONFINITE;
+
+    // ---- v_{n+1} = (x_{n+1} - x_n)/h and post-convergence dissipation (Sec. 2.1.4)
+    const T inv_h = T(1) / h;
+    double sums[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) sums[q] = 0.0;
+    if (!nonfinite) {
+        for (int i = tid; i < n; i += NT) {
+            const double m = (double)__ldg(&tp.mass[i]);
+            double xr[3], vr[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xr[c] = (double)XN[c * np + i] + (double)u[c * np + i];
+                vr[c] = (double)(u[c * np + i] * inv_h);
+            }
+            sums[0] += m;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sums[1 + c] += m * xr[c];
+                sums[4 + c] += m * vr[c];
+            }
+            sums[7] += m * (xr[1] * vr[2] - xr[2] * vr[1]);
+            sums[8] += m * (xr[2] * vr[0] - xr[0] * vr[2]);
+            sums[9] += m * (xr[0] * vr[1] - xr[1] * vr[0]);
+            sums[10] += m * xr[0] * xr[0];
+            sums[11] += m * xr[1] * xr[1];
+            sums[12] += m * xr[2] * xr[2];
+            sums[13] += m * xr[0] * xr[1];
+            sums[14] += m * xr[0] * xr[2];
+            sums[15] += m * xr[1] * xr[2];
+        }
+    }
+    block_sum<16>(sums, red);
+    double w[3] = {0.0, 0.0, 0.0}, xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
+    if (!nonfinite) {
+        const double Mt = sums[0];
+        for (int c = 0; c < 3; ++c) {
+            xc[c] = sums[1 + c] / Mt;
+            vc[c] = sums[4 + c] / Mt;
+        }
+        // angular momentum and inertia tensor about the centre of mass
+        const double L0 = sums[7] - Mt * (xc[1] * vc[2] - xc[2] * vc[1]);
+        const double L1 = sums[8] - Mt * (xc[2] * vc[0] - xc[0] * vc[2]);
+        const double L2 = sums[9] - Mt * (xc[0] * vc[1] - xc[1] * vc[0]);
+        const double Sxx = sums[10] - Mt * xc[0] * xc[0], Syy = sums[11] - Mt * xc[1] * xc[1],
+                     Szz = sums[12] - Mt * xc[2] * xc[2];
+        const double Sxy = sums[13] - Mt * xc[0] * xc[1], Sxz = sums[14] - Mt * xc[0] * xc[2],
+                     Syz = sums[15] - Mt * xc[1] * xc[2];
+        const double I00 = Syy + Szz, I11 = Sxx + Szz, I22 = Sxx + Syy;
+        const double I01 = -Sxy, I02 = -Sxz, I12 = -Syz;
+        const double c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
+        const double c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
+        const double det = I00 * c00 + I01 * c01 + I02 * c02;
+        w[0] = (c00 * L0 + c01 * L1 + c02 * L2) / det;
+        w[1] = (c01 * L0 + c11 * L1 + c12 * L2) / det;
+        w[2] = (c02 * L0 + c12 * L1 + c22 * L2) / det;
+    }
+    const double kap = (double)tp.kappa;
+    for (int i = tid; i < n; i += NT) {
+        T* x = a.x + so;
+        T* v = a.v + so;
+        if (nonfinite) {
+            for (int c = 0; c < 3; ++c) v[c * n + i] = T(0);
+            continue;
+        }
+        double r[3];
+        for (int c = 0; c < 3; ++c) r[c] = (double)XN[c * np + i] + (double)u[c * np + i] - xc[c];
+        const double wr[3] = {w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2], w[0] * r[1] - w[1] * r[0]};
+        for (int c = 0; c < 3; ++c) {
+            const T uc = u[c * np + i];
+            const double vv = (double)(uc * inv_h);
+            v[c * n + i] = (T)(vv + kap * (vc[c] + wr[c] - vv));
+            x[c * n + i] = x[c * n + i] + uc;
+        }
+    }
+    if (tid == 0 && a.stats) {
+        npfem_cell_stats st;
+        st.iterations = iters;
+        st.evaluations = evals;
+        st.status = status;
+        st.residual = (float)res;
+        st.objective = E;
+        st.volume = ev.V;
+        a.stats[item] = st;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) cell_kernel(const __grid_constant__ LaunchArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&a.work[0], 1u);
+        __syncthreads();
+        const long long item = s_item;
+        __syncthreads();
+        if (item >= a.total_cells) break;
+        int gi = 0;
+        while (gi + 1 < a.n_groups && item >= a.g[gi + 1].cell_begin) ++gi;
+        solve_cell<T>(a, a.g[gi], item - a.g[gi].cell_begin, item, smem);
+    }
+    // the last block to finish resets the work counters for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.work[1], 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&a.work[0], 0u);
+            atomicExch(&a.work[1], 0u);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t set_cell_kernel_smem(int bytes)
+{
+    return cudaFuncSetAttribute(cell_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename T>
+cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s)
+{
+    cell_kernel<T><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t set_cell_kernel_smem<float>(int);
+template cudaError_t set_cell_kernel_smem<double>(int);
+template cudaError_t launch_cells<float>(const LaunchArgs<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_cells<double>(const LaunchArgs<double>&, int, int, int, cudaStream_t);
+
+}  // namespace npfem

@@ -1,0 +1,177 @@
+"""ctypes binding of libnpfem.so (include/npfem.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; there is no CPU path.
+Device arrays may be passed as torch tensors (their data_ptr is used) or as raw
+integer addresses.  Errors raise NpfemError with the library's message."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+CELL_STATUS = {0: "OK", 1: "MAXITER", 2: "LINESEARCH_FAIL", 3: "NONFINITE"}
+MATERIAL_ORDER = ("B", "C", "D", "k_bend", "k_vol", "k_mat_hess", "density", "alpha_D", "beta_D", "kappa")
+
+
+class NpfemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"npfem error {code}: {msg}")
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("tris", C.c_void_p), ("rest_xyz", C.c_void_p)]
+
+
+class Material(C.Structure):
+    _fields_ = [(k, C.c_double) for k in MATERIAL_ORDER]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("lbfgs_m", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("c1", C.c_double), ("c2", C.c_double), ("max_halvings", C.c_int32), ("fixed_alpha", C.c_int32),
+                ("equal_mass", C.c_int32), ("armijo_noise", C.c_double)]
+
+
+class CellStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("evaluations", C.c_int32), ("status", C.c_int32),
+                ("residual", C.c_float), ("objective", C.c_double), ("volume", C.c_double)]
+
+
+CELL_STATS_DTYPE = np.dtype([("iterations", "<i4"), ("evaluations", "<i4"), ("status", "<i4"),
+                             ("residual", "<f4"), ("objective", "<f8"), ("volume", "<f8")])
+
+_lib = None
+EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", "npfem_step_host", "npfem_eval",
+           "npfem_get_inverse", "npfem_get_rest_info", "npfem_last_error")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libnpfem.so (building it first if a source is newer); raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, i32 = C.c_void_p, C.c_int
+        L.npfem_default_opts.argtypes = [C.POINTER(Opts)]
+        L.npfem_default_opts.restype = None
+        L.npfem_create.argtypes = [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Opts), C.c_double, i32, C.POINTER(vp)]
+        L.npfem_destroy.argtypes = [vp]
+        L.npfem_step.argtypes = [C.POINTER(vp), i32, C.POINTER(C.c_int32), vp, vp, vp, C.c_double, vp, vp]
+        L.npfem_step_host.argtypes = [vp, i32, vp, vp, vp, C.c_double, vp, vp]
+        L.npfem_eval.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        L.npfem_get_inverse.argtypes = [vp, vp]
+        L.npfem_get_rest_info.argtypes = [vp, vp, vp]
+        L.npfem_last_error.restype = C.c_char_p
+        L.npfem_last_error.argtypes = []
+        for name in EXPORTS:
+            if name not in ("npfem_default_opts", "npfem_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise NpfemError(rc, lib().npfem_last_error().decode())
+
+
+def _addr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(f"cannot take the address of {type(t)}")
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().npfem_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PREC[v]
+        setattr(o, k, v)
+    return o
+
+
+def material(**kw) -> Material:
+    from .workloads import DEFAULT_MATERIAL
+    d = dict(DEFAULT_MATERIAL)
+    d.update(kw)
+    return Material(*[float(d[k]) for k in MATERIAL_ORDER])
+
+
+class Handle:
+    """One mesh topology on one device (npfem_create / npfem_destroy)."""
+
+    def __init__(self, rest: np.ndarray, tris: np.ndarray, mat: Material | None = None, opts: Opts | None = None,
+                 dt: float = 0.1, device: int = 0):
+        self._rest = np.ascontiguousarray(rest, dtype=np.float64)
+        self._tris = np.ascontiguousarray(tris, dtype=np.int32)
+        self.n = self._rest.shape[0]
+        self.nt = self._tris.shape[0]
+        self.opts = opts or default_opts()
+        self.material = mat or material()
+        self.dt = float(dt)
+        self.device = device
+        self.precision = int(self.opts.precision)
+        m = Mesh(self.n, self.nt, self._tris.ctypes.data, self._rest.ctypes.data)
+        h = C.c_void_p()
+        _check(lib().npfem_create(C.byref(m), C.byref(self.material), C.byref(self.opts), self.dt, device, C.byref(h)))
+        self._h = h
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().npfem_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def inverse(self) -> np.ndarray:
+        out = np.zeros((self.n, self.n))
+        _check(lib().npfem_get_inverse(self._h, out.ctypes.data))
+        return out
+
+    def rest_info(self):
+        m = np.zeros(self.n)
+        s = np.zeros(4)
+        _check(lib().npfem_get_rest_info(self._h, m.ctypes.data, s.ctypes.data))
+        return m, dict(V0=s[0], A0=s[1], lbar=s[2], mtotal=s[3])
+
+    def eval(self, n_cells: int, x, y, grad, parts, stream=None):
+        _check(lib().npfem_eval(self._h, n_cells, _addr(x), _addr(y), _addr(grad), _addr(parts), _addr(stream)))
+
+    def step_host(self, x: np.ndarray, v: np.ndarray, f: np.ndarray, stats: np.ndarray | None = None, stream=None):
+        """One step of x, v (host SoA arrays, updated in place) with host forces f."""
+        n_cells = x.shape[0]
+        _check(lib().npfem_step_host(self._h, n_cells, x.ctypes.data, v.ctypes.data, f.ctypes.data, self.dt,
+                                     _addr(stream), None if stats is None else stats.ctypes.data))
+
+
+def step(handles, cells_per_group, x, v, f, dt: float, stream=None, stats=None):
+    """npfem_step over one or more handles (device SoA state, updated in place)."""
+    handles = list(handles)
+    arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
+    _check(lib().npfem_step(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), _addr(stream),
+                            _addr(stats)))

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (called through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances (stated per test):
+  * FP64 GPU path, fixed iteration count, exact Armijo test: max_i |dx_i| / lbar <= 1e-10.
+  * FP32 GPU path at tolerance 1e-6: max_i |dx_i| / lbar <= 1e-5, plus the FP32
+    storage rounding of x_{n+1} (half an ulp of the largest coordinate) where cells
+    sit far from the origin.
+"""
+import numpy as np
+import pytest
+
+from helpers import DT, fp32_store_allowance, gpu_step_device, max_rel_disp, oracle_model, oracle_steps, population32
+from paper_1903_06479_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def npfem():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_06479_gb300 import npfem as N
+    N.lib()
+    return N
+
+
+def make_handle(N, n_verts, precision="fp32", **kw):
+    rest, tris = W.discocyte(n_verts)
+    mat = {k: kw.pop(k) for k in list(kw) if k in W.DEFAULT_MATERIAL}
+    opts = N.default_opts(precision=precision, **kw)
+    return N.Handle(rest, tris, N.material(**mat), opts, dt=DT)
+
+
+# ---------------------------------------------------------------------------------
+# setup: rest tables and the FP64 inverse
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("n_verts", [258, 642])
+def test_setup_matches_oracle(npfem, n_verts):
+    h = make_handle(npfem, n_verts, "fp64")
+    m, rest, tris = oracle_model(n_verts)
+    masses, sc = h.rest_info()
+    assert np.allclose(masses, m.masses(), rtol=1e-12)
+    assert abs(sc["V0"] - m.V0) < 1e-12 * m.V0 and abs(sc["A0"] - m.A0) < 1e-12 * m.A0
+    assert abs(sc["lbar"] - m.lbar) < 1e-12 * m.lbar
+    Ainv = h.inverse()
+    H = m.hessian()
+    assert np.abs(Ainv @ H - np.eye(n_verts)).max() < 1e-11
+    assert np.abs(Ainv - Ainv.T).max() == 0.0
+
+
+# ---------------------------------------------------------------------------------
+# objective and gradient, energy by energy
+# ---------------------------------------------------------------------------------
+def _eval_case(n_verts, cells, seed):
+    m, rest, tris = oracle_model(n_verts)
+    rng = np.random.default_rng(seed)
+    x = W.place_cells(rest, rng, cells, box=30.0)
+    x = x + 0.03 * m.lbar * rng.standard_normal(x.shape)
+    x[0] = x[0] * 1.02  # one cell with a volume error
+    y = x + 0.002 * m.lbar * rng.standard_normal(x.shape)
+    return m, x, y
+
+
+@pytest.mark.parametrize("prec,tol_e,tol_g", [("fp64", 1e-11, 1e-10), ("fp32", 3e-5, 2e-4)])
+@pytest.mark.parametrize("n_verts", [258, 642])
+def test_eval_parity(npfem, prec, tol_e, tol_g, n_verts):
+    import torch
+    h = make_handle(npfem, n_verts, prec)
+    cells = 6
+    m, x, y = _eval_case(n_verts, cells, 3 + n_verts)
+    td = torch.float64 if prec == "fp64" else torch.float32
+    if prec == "fp32":
+        x = x.astype(np.float32).astype(np.float64)
+        y = y.astype(np.float32).astype(np.float64)
+    xs = torch.tensor(W.to_soa(x), dtype=td, device="cuda")
+    ys = torch.tensor(W.to_soa(y), dtype=td, device="cuda")
+    g = torch.zeros_like(xs)
+    parts = torch.zeros((cells, 8), dtype=torch.float64, device="cuda")
+    h.eval(cells, xs, ys, g, parts)
+    torch.cuda.synchronize()
+    g = W.from_soa(g.double().cpu().numpy())
+    parts = parts.cpu().numpy()
+    for c in range(cells):
+        E, G, P = m.objective(x[c], y[c])
+        # parts: inertia, area, skalak, bend, volume energy, V, g, r
+        for q, name in [(0, "inertia"), (1, "area"), (2, "skalak"), (3, "bend")]:
+            assert abs(parts[c, q] - P[q]) <= tol_e * max(abs(P[q]), 1e-3 * abs(E)), (c, name, parts[c, q], P[q])
+        assert abs(parts[c, 5] - P[5]) <= tol_e * P[5] * 10
+        assert abs(parts[c, 6] - E) <= tol_e * abs(E)
+        assert np.abs(g[c] - G).max() <= tol_g * np.abs(G).max(), (c, np.abs(g[c] - G).max(), np.abs(G).max())
+        assert abs(parts[c, 7] - m.residual(G)) <= tol_g * m.residual(G)
+
+
+# ---------------------------------------------------------------------------------
+# one time step
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("n_verts,cells", [(258, 4), (642, 5)])
+def test_step_parity_fp64_fixed_iterations(npfem, n_verts, cells):
+    # tol = 0 and a fixed cap of 8 iterations: both sides take the same steps
+    h = make_handle(npfem, n_verts, "fp64", tol=0.0, max_iter=8, armijo_noise=0.0)
+    m, _, _ = oracle_model(n_verts)
+    p = population32(n_verts, cells, seed=n_verts, forces="shear", noise_pN=1.0)
+    xo, vo, st = oracle_steps(m, p["x"], p["v"], p["f"], tol=0.0, max_iter=8)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"], dtype="float64")
+    assert max_rel_disp(xg, xo, m.lbar) <= 1e-10
+    assert max_rel_disp(DT * vg, DT * vo, m.lbar) <= 1e-10
+    for c in range(cells):
+        assert sg["iterations"][c] == st[c].iterations
+
+
+@pytest.mark.parametrize("n_verts,cells,seed", [(258, 6, 1), (642, 8, 2)])
+def test_step_parity_fp32_at_tolerance(npfem, n_verts, cells, seed):
+    h = make_handle(npfem, n_verts, "fp32", tol=1e-6)
+    m, _, _ = oracle_model(n_verts)
+    p = population32(n_verts, cells, seed=seed, forces="shear", noise_pN=0.5)
+    xo, vo, st = oracle_steps(m, p["x"], p["v"], p["f"], tol=1e-10, max_iter=200)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    assert all(s == 0 for s in sg["status"]), sg
+    assert (sg["residual"] <= 1e-6).all()
+    allow = fp32_store_allowance(p["x"], m.lbar)
+    assert max_rel_disp(xg, xo, m.lbar) <= 1e-5 + allow
+    assert max_rel_disp(DT * vg, DT * vo, m.lbar) <= 1e-5
+
+
+def test_step_parity_fp32_near_origin_strict(npfem):
+    # cells within 10 um of the origin: the storage rounding is < 1e-6 lbar
+    h = make_handle(npfem, 642, "fp32", tol=1e-6)
+    m, _, _ = oracle_model(642)
+    p = population32(642, 4, seed=9, forces="noise", noise_pN=2.0, box=2.0)
+    xo, vo, st = oracle_steps(m, p["x"], p["v"], p["f"], tol=1e-10, max_iter=200)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    assert max_rel_disp(xg, xo, m.lbar) <= 1e-5
+
+
+def test_several_steps_fp32(npfem):
+    h = make_handle(npfem, 642, "fp32", tol=1e-6)
+    m, _, _ = oracle_model(642)
+    p = population32(642, 3, seed=4, forces="shear", gamma_fixed=1000.0, noise_pN=2.0, box=4.0)
+    xo, vo, _ = oracle_steps(m, p["x"], p["v"], p["f"], steps=5, tol=1e-10, max_iter=200)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"], steps=5)
+    assert max_rel_disp(xg, xo, m.lbar) <= 5e-5
+
+
+def test_mixed_resolutions_one_launch(npfem):
+    import torch
+    sizes = [(2562, 2), (642, 3), (258, 3)]
+    hs, ms, pops = [], [], []
+    for k, (nv, c) in enumerate(sizes):
+        hs.append(make_handle(npfem, nv, "fp32", tol=1e-6))
+        ms.append(oracle_model(nv)[0])
+        pops.append(population32(nv, c, seed=20 + k, forces="shear", noise_pN=0.5, box=6.0))
+    flat = lambda key: np.concatenate([W.to_soa(p[key]).ravel() for p in pops])
+    xs = torch.tensor(flat("x"), dtype=torch.float32, device="cuda")
+    vs = torch.tensor(flat("v"), dtype=torch.float32, device="cuda")
+    fs = torch.tensor(flat("f"), dtype=torch.float32, device="cuda")
+    total = sum(c for _, c in sizes)
+    st = torch.zeros((total, 32), dtype=torch.uint8, device="cuda")
+    npfem.step(hs, [c for _, c in sizes], xs, vs, fs, DT, stats=st)
+    torch.cuda.synchronize()
+    sg = st.cpu().numpy().view(npfem.CELL_STATS_DTYPE).reshape(total)
+    assert (sg["status"] == 0).all()
+    xg = xs.double().cpu().numpy()
+    off = 0
+    for (nv, c), m, p in zip(sizes, ms, pops):
+        xo, _, _ = oracle_steps(m, p["x"], p["v"], p["f"], tol=1e-10, max_iter=200)
+        part = W.from_soa(xg[off:off + 3 * nv * c].reshape(c, 3, nv))
+        off += 3 * nv * c
+        assert max_rel_disp(part, xo, m.lbar) <= 1e-5 + fp32_store_allowance(p["x"], m.lbar)
+
+
+def test_step_host_matches_device(npfem):
+    h = make_handle(npfem, 642, "fp32", tol=1e-6)
+    p = population32(642, 4, seed=5)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    xh = W.to_soa(p["x"]).astype(np.float32)
+    vh = W.to_soa(p["v"]).astype(np.float32)
+    fh = W.to_soa(p["f"]).astype(np.float32)
+    st = np.zeros(4, dtype=npfem.CELL_STATS_DTYPE)
+    h.step_host(xh, vh, fh, st)
+    assert np.array_equal(W.from_soa(xh.astype(np.float64)), xg)
+    assert np.array_equal(st["iterations"], sg["iterations"])
+
+
+# ---------------------------------------------------------------------------------
+# edge cases and failure reporting (host-made failures only)
+# ---------------------------------------------------------------------------------
+def test_zero_cells_and_invalid_args(npfem):
+    import torch
+    h = make_handle(npfem, 258, "fp32")
+    x = torch.zeros(3 * 258, device="cuda")
+    npfem.step([h], [0], x, x, x, DT)  # no work, no error
+    with pytest.raises(npfem.NpfemError) as e:
+        npfem.step([h], [1], x, x, x, DT * 2)
+    assert e.value.code == -1
+    rest, tris = W.discocyte(258)
+    with pytest.raises(npfem.NpfemError) as e:
+        npfem.Handle(rest, tris[:-1], opts=npfem.default_opts())  # open mesh
+    assert e.value.code == -2
+    bad = tris.copy()
+    bad[:, [1, 2]] = bad[:, [2, 1]]  # clockwise: negative rest volume
+    with pytest.raises(npfem.NpfemError) as e:
+        npfem.Handle(rest, bad, opts=npfem.default_opts())
+    assert e.value.code == -2
+
+
+def test_nonfinite_force_flags_only_that_cell(npfem):
+    h = make_handle(npfem, 642, "fp32", tol=1e-6)
+    p = population32(642, 3, seed=6)
+    p["f"][1, 7, 0] = np.nan
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    assert list(sg["status"]) == [0, 3, 0]
+    assert np.array_equal(xg[1], p["x"][1]) and (vg[1] == 0).all()
+    assert np.isfinite(xg).all()
+
+
+def test_iteration_cap_reports_maxiter(npfem):
+    h = make_handle(npfem, 642, "fp32", tol=1e-12, max_iter=1)
+    p = population32(642, 2, seed=7, forces="noise", noise_pN=50.0)
+    _, _, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    assert (sg["status"] == 1).all() and (sg["iterations"] == 1).all()
+
+
+# ---------------------------------------------------------------------------------
+# full size: 16384 cells of 642 vertices in the benchmark's launch configuration,
+# checked on sampled cells against the oracle and by invariants on all cells
+# ---------------------------------------------------------------------------------
+def test_full_size_sampled(npfem):
+    h = make_handle(npfem, 642, "fp32", tol=1e-6)
+    m, _, _ = oracle_model(642)
+    p = population32(642, 16384, seed=3, forces="shear", gamma_fixed=1000.0, noise_pN=2.0)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    assert (sg["status"] == 0).all() and (sg["residual"] <= 1e-6).all()
+    assert np.isfinite(xg).all() and np.isfinite(vg).all()
+    Mv = m.masses()
+    # sum m (v_{n+1} - v_n) = h sum F_ext - h sum grad g (internal forces sum to zero,
+    # the post step conserves momentum), and |h sum grad g| <= n r lbar max(m) / h
+    P_gpu = (Mv[None, :, None] * vg).sum(1)
+    P_exp = (Mv[None, :, None] * p["v"]).sum(1) + DT * p["f"].sum(1)
+    bound = 642 * sg["residual"].astype(np.float64) * m.lbar * Mv.max() / DT
+    assert (np.abs(P_gpu - P_exp).max(1) <= bound + 1e-4 * np.abs(P_exp).max(1)).all()
+    sample = np.random.default_rng(0).choice(16384, 8, replace=False)
+    xo, vo, _ = oracle_steps(m, p["x"][sample], p["v"][sample], p["f"][sample], tol=1e-10, max_iter=200)
+    assert max_rel_disp(xg[sample], xo, m.lbar) <= 1e-5 + fp32_store_allowance(p["x"], m.lbar)
