@@ -25,6 +25,12 @@ int fail(int code, const std::string& msg)
     return code;
 }
 
+}  // namespace
+
+int npfem::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+namespace {
+
 #define NPFEM_CUDA(call)                                                                               \
     do {                                                                                               \
         cudaError_t e_ = (call);                                                                       \
@@ -50,60 +56,6 @@ struct DeviceGuard {
 
 }  // namespace
 
-struct npfem_handle {
-    int device = 0;
-    int precision = NPFEM_PREC_FP32;
-    double dt = 0.0;
-    npfem_opts opts{};
-    npfem_material mat{};
-    HostTopo host;
-    int n = 0, nt = 0, n_pad = 0;
-    std::vector<void*> allocs;  // every device allocation owned by the handle
-    TopoDev<float> tf{};
-    TopoDev<double> td{};
-    double* ainv64 = nullptr;   // n x n FP64 inverse (unpadded)
-    // launch resources (used when this handle is the first of a step call)
-    unsigned int* work = nullptr;
-    char* scratch = nullptr;
-    size_t scratch_bytes = 0;
-    int sm_count = 0, smem_optin = 0;
-    int threads = 512;
-    // buffers of npfem_step_host
-    void* hx = nullptr;
-    void* hv = nullptr;
-    void* hf = nullptr;
-    npfem_cell_stats* hstats = nullptr;
-    size_t host_cells = 0;
-    std::mutex mu;
-
-    template <typename X>
-    X* alloc(size_t count, int* err)
-    {
-        void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(X) + 16);
-        if (e != cudaSuccess) {
-            *err = fail(e == cudaErrorMemoryAllocation ? NPFEM_ERR_OOM : NPFEM_ERR_CUDA,
-                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
-            return nullptr;
-        }
-        allocs.push_back(p);
-        return static_cast<X*>(p);
-    }
-    void release()
-    {
-        for (void* p : allocs) cudaFree(p);
-        allocs.clear();
-        if (scratch) cudaFree(scratch);
-        scratch = nullptr;
-        scratch_bytes = 0;
-        if (hx) cudaFree(hx);
-        if (hv) cudaFree(hv);
-        if (hf) cudaFree(hf);
-        if (hstats) cudaFree(hstats);
-        hx = hv = hf = nullptr;
-        hstats = nullptr;
-    }
-};
 
 namespace {
 
@@ -180,35 +132,6 @@ int check_opts(const npfem_opts* o)
         !(o->armijo_noise >= 0.0))
         return fail(NPFEM_ERR_INVALID_ARG, "opts: need tol >= 0, 0 < c1 < c2 < 1, armijo_noise >= 0");
     return 0;
-}
-
-// Places the per-cell vectors: shared memory in priority order while it fits, the
-// rest in a per-block global slot.  Returns the smem bytes (after kFixedSmem).
-template <typename T>
-void place_vectors(GroupDesc<T>* g, int n_pad, int m, int smem_budget, long long* slot_bytes)
-{
-    const int vb = 3 * n_pad * (int)sizeof(T);
-    int order[kMaxVecs], nv = 0;
-    const int base[kNumBaseVecs] = {V_XN, V_U, V_UT, V_G, V_GT, V_GC, V_UY, V_D};
-    for (int q = 0; q < kNumBaseVecs; ++q) order[nv++] = base[q];
-    for (int q = 0; q < m; ++q) {
-        order[nv++] = V_SBASE + q;
-        order[nv++] = V_SBASE + m + q;
-    }
-    int used = 0;
-    long long gl = 0;
-    for (int q = 0; q < kMaxVecs; ++q) g->loc[q] = 0;
-    for (int q = 0; q < nv; ++q) {
-        if (used + vb <= smem_budget) {
-            g->loc[order[q]] = used;
-            used += vb;
-        } else {
-            g->loc[order[q]] = -(int)gl - 1;
-            gl += vb;
-        }
-    }
-    g->smem_bytes = used;
-    *slot_bytes = gl;
 }
 
 template <typename T>

@@ -11,6 +11,11 @@
 // The solve runs on the increment u = x - x_n in cell-local coordinates (origin at
 // the cell's first vertex) so that FP32 keeps the small per-step displacements:
 // edges are (X_j - X_i) + (u_j - u_i) and the enclosed volume is V(x_n) + dV(u).
+//
+// FP64 throughput is a small fraction of FP32 on this part, so the FP32 path does
+// no per-thread FP64 arithmetic: block sums are compensated FP32 pairs (error-free
+// two-sum), and the few scalar FP64 operations per reduction run on one thread
+// and are broadcast through shared memory.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -36,25 +41,94 @@ struct Unit<double> {
     static constexpr double tiny = 1.0e-300;
 };
 
-// Block-wide sum of K doubles; every thread receives the totals in the same order.
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* red)
+// Compensated sum (hi + lo) built from error-free two-sums.
+template <typename T>
+struct Acc {
+    T hi, lo;
+    __device__ __forceinline__ Acc() : hi(T(0)), lo(T(0)) {}
+    __device__ __forceinline__ void add(T x)
+    {
+        const T s = hi + x;
+        const T bb = s - hi;
+        lo += (hi - (s - bb)) + (x - bb);
+        hi = s;
+    }
+    __device__ __forceinline__ void merge(T h2, T l2)
+    {
+        add(h2);
+        lo += l2;
+    }
+};
+
+// Per-cell scalars shared by the block (after the 8 KB of reduction partials).
+struct CellShared {
+    double out[16];          // results of the last block_reduce
+    double V, E, Ein, Earea, Esk, Ebend, Evol, res, noise;
+    double rho[kMaxHistory];
+    double alpha[kMaxHistory];
+    double post[12];         // centre of mass, its velocity, angular velocity
+    double volc;
+    int bad;
+    int accept;
+    int push;
+};
+static_assert(sizeof(CellShared) <= kFixedSmem - 8192, "CellShared does not fit");
+
+__device__ __forceinline__ CellShared* cell_shared(unsigned char* smem)
 {
+    return reinterpret_cast<CellShared*>(smem + 8192);
+}
+
+// Sums K compensated accumulators over the block.  Thread 0 writes the totals to
+// sh->out[] and then runs epi(sh) before the closing barrier, so every thread sees
+// the totals and whatever the epilogue derived from them.
+struct NoEpi {
+    __device__ __forceinline__ void operator()(CellShared*) const {}
+};
+
+template <typename T, int K, typename Epi = NoEpi>
+__device__ __forceinline__ void block_reduce(Acc<T> (&a)[K], unsigned char* smem, Epi epi = Epi())
+{
+    T* red = reinterpret_cast<T*>(smem);  // [32 warps][K][2]
+    CellShared* sh = cell_shared(smem);
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const T h2 = __shfl_xor_sync(kFull, a[k].hi, o);
+            const T l2 = __shfl_xor_sync(kFull, a[k].lo, o);
+            a[k].merge(h2, l2);
+        }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[w * K + k] = v[k];
+        for (int k = 0; k < K; ++k) {
+            red[(w * K + k) * 2] = a[k].hi;
+            red[(w * K + k) * 2 + 1] = a[k].lo;
+        }
     }
     __syncthreads();
+    if (w == 0) {
+        Acc<T> b[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double s = 0.0;
-        for (int q = 0; q < nw; ++q) s += red[q * K + k];
-        v[k] = s;
+        for (int k = 0; k < K; ++k)
+            if (lane < nw) {
+                b[k].hi = red[(lane * K + k) * 2];
+                b[k].lo = red[(lane * K + k) * 2 + 1];
+            }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T h2 = __shfl_xor_sync(kFull, b[k].hi, o);
+                const T l2 = __shfl_xor_sync(kFull, b[k].lo, o);
+                b[k].merge(h2, l2);
+            }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) sh->out[k] = (double)b[k].hi + (double)b[k].lo;
+            epi(sh);
+        }
     }
     __syncthreads();
 }
@@ -73,16 +147,16 @@ __device__ __forceinline__ T sl2_t(T e1, T e2)
     T t = T(0.5) * (e1 - e2);
     t = t < lo ? lo : (t > hi ? hi : t);
     for (int it = 0; it < 60; ++it) {
-        T a1 = T(1) + t;
-        T a2 = a1 * a1;
-        T tm = t - e1;
-        T ph = tm * a2 * a1 + t * (T(1) + e2) + e2;
+        const T a1 = T(1) + t;
+        const T a2 = a1 * a1;
+        const T tm = t - e1;
+        const T ph = tm * a2 * a1 + t * (T(1) + e2) + e2;
         if (ph == T(0)) break;
         if (ph < T(0)) lo = t; else hi = t;
-        T dph = a2 * a1 + T(3) * tm * a2 + (T(1) + e2);
+        const T dph = a2 * a1 + T(3) * tm * a2 + (T(1) + e2);
         T tn = t - ph / dph;
         if (!(tn > lo && tn < hi)) tn = T(0.5) * (lo + hi);
-        T step = tn - t;
+        const T step = tn - t;
         t = tn;
         if (fabs(step) <= Unit<T>::sl2_rel * (fabs(t) + fabs(e1) + fabs(e2)) + Unit<T>::tiny || hi - lo <= T(0)) break;
     }
@@ -90,26 +164,20 @@ __device__ __forceinline__ T sl2_t(T e1, T e2)
 }
 
 template <typename T>
-struct EvalOut {
-    double E, Earea, Esk, Ebend, Evol, Ein, V, res, noise;
-    bool bad;
-};
-
-template <typename T>
 __device__ __forceinline__ T* vec_ptr(const GroupDesc<T>& gd, unsigned char* smem, char* slot, int v)
 {
-    int l = gd.loc[v];
+    const int l = gd.loc[v];
     return l >= 0 ? reinterpret_cast<T*>(smem + kFixedSmem + l) : reinterpret_cast<T*>(slot + (-(long long)l - 1));
 }
 
 // Volume of the cell at x_n in local coordinates: V = sum_t X_i . (E1 x E2) / 6.
 template <typename T>
-__device__ double volume_at_xn(const TopoDev<T>& tp, const T* XN, double* red)
+__device__ void volume_at_xn(const TopoDev<T>& tp, const T* XN, unsigned char* smem)
 {
     const int np = tp.n_pad;
-    double acc = 0.0;
+    Acc<T> acc[1];
     for (int t = threadIdx.x; t < tp.nt; t += blockDim.x) {
-        ushort4 tv = __ldg(&tp.tri[t]);
+        const ushort4 tv = __ldg(&tp.tri[t]);
         T Xi[3], E1[3], E2[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -117,23 +185,25 @@ __device__ double volume_at_xn(const TopoDev<T>& tp, const T* XN, double* red)
             E1[c] = XN[c * np + tv.y] - Xi[c];
             E2[c] = XN[c * np + tv.z] - Xi[c];
         }
-        T cx = E1[1] * E2[2] - E1[2] * E2[1], cy = E1[2] * E2[0] - E1[0] * E2[2], cz = E1[0] * E2[1] - E1[1] * E2[0];
-        acc += (double)(Xi[0] * cx + Xi[1] * cy + Xi[2] * cz);
+        const T cx = E1[1] * E2[2] - E1[2] * E2[1], cy = E1[2] * E2[0] - E1[0] * E2[2],
+                cz = E1[0] * E2[1] - E1[1] * E2[0];
+        acc[0].add(Xi[0] * cx + Xi[1] * cy + Xi[2] * cz);
     }
-    double v[1] = {acc};
-    block_sum<1>(v, red);
-    return v[0] / 6.0;
+    block_reduce<T, 1>(acc, smem, [](CellShared* sh) { sh->V = sh->out[0] / 6.0; });
 }
 
 // Objective g and gradient at x_n + U (Eq. GeneralizedObjectiveFunction and its
 // derivative): inertia, local area preservation and bending (projective dynamics
 // gradients), global volume conservation (PD gradient with the linearised
-// projection), modified Skalak (first Piola-Kirchhoff forces).
+// projection), modified Skalak (first Piola-Kirchhoff forces).  Results are left in
+// cell_shared(smem): E, its parts, V, residual r, rounding estimate of E, bad flag.
+// Vn is the volume at x_n (held by the caller).
 template <typename T>
-__device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T* UY, T* Gout, T* GC,
-                               double Vn, double* red)
+__device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T* UY, T* Gout, T* GC, double Vn,
+                         unsigned char* smem)
 {
     const int n = tp.n, np = tp.n_pad, N3 = 3 * np, tid = threadIdx.x, NT = blockDim.x;
+    CellShared* sh = cell_shared(smem);
     for (int e = tid; e < N3; e += NT) {
         Gout[e] = T(0);
         GC[e] = T(0);
@@ -142,18 +212,17 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
 
     const T Cs = tp.C, Bs = tp.B, Ds = tp.Dsk;
     const T sixth = T(1) / T(6);
-    double eA = 0.0, eS = 0.0, dV = 0.0, noise = 0.0;
-    int bad = 0;
+    Acc<T> acc[7];  // area, skalak, bending, dV*6, |grad C|^2, noise, bad
     for (int t = tid; t < tp.nt; t += NT) {
         const ushort4 tv = __ldg(&tp.tri[t]);
         const int i = tv.x, j = tv.y, k = tv.z;
         T Di0, Di1, Di2, Di3;
         if constexpr (sizeof(T) == 4) {
-            float4 d4 = __ldg(reinterpret_cast<const float4*>(tp.dminv) + t);
+            const float4 d4 = __ldg(reinterpret_cast<const float4*>(tp.dminv) + t);
             Di0 = d4.x; Di1 = d4.y; Di2 = d4.z; Di3 = d4.w;
         } else {
-            double2 a2 = __ldg(reinterpret_cast<const double2*>(tp.dminv) + 2 * t);
-            double2 b2 = __ldg(reinterpret_cast<const double2*>(tp.dminv) + 2 * t + 1);
+            const double2 a2 = __ldg(reinterpret_cast<const double2*>(tp.dminv) + 2 * t);
+            const double2 b2 = __ldg(reinterpret_cast<const double2*>(tp.dminv) + 2 * t + 1);
             Di0 = a2.x; Di1 = a2.y; Di2 = b2.x; Di3 = b2.y;
         }
         const T Wt = __ldg(&tp.W[t]);
@@ -188,7 +257,7 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
         const T q2 = T(1) + m2;
         const T s2 = q2 > T(0) ? sqrt(q2) : T(0);
         if (!(s2 > T(1e-6) * s1) || !(s1 < T(1e30))) {
-            bad = 1;
+            acc[6].add(T(1));
             continue;
         }
         const T e1s = m1 / (s1 + T(1)), e2s = m2 / (s2 + T(1));
@@ -196,16 +265,17 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
         const T tsl = sl2_t(e1s, e2s);
         const T dd1 = e1s - tsl, dd2 = e2s + tsl / (T(1) + tsl);
         // modified Skalak, f(s) = B/8 (s^2 - 1)^2 + D/4 (s - 1)^4, written in e = s - 1
-        const T f1 = T(0.125) * Bs * (e1s * (T(2) + e1s)) * (e1s * (T(2) + e1s)) + T(0.25) * Ds * e1s * e1s * e1s * e1s;
-        const T f2 = T(0.125) * Bs * (e2s * (T(2) + e2s)) * (e2s * (T(2) + e2s)) + T(0.25) * Ds * e2s * e2s * e2s * e2s;
-        const T fp1 = T(0.5) * Bs * (T(1) + e1s) * e1s * (T(2) + e1s) + Ds * e1s * e1s * e1s;
-        const T fp2 = T(0.5) * Bs * (T(1) + e2s) * e2s * (T(2) + e2s) + Ds * e2s * e2s * e2s;
-        eA += (double)(T(0.5) * Cs * Wt * (dd1 * dd1 + dd2 * dd2));
-        eS += (double)(Wt * (f1 + f2));
+        const T q1 = e1s * (T(2) + e1s), q2b = e2s * (T(2) + e2s);
+        const T f1 = T(0.125) * Bs * q1 * q1 + T(0.25) * Ds * e1s * e1s * e1s * e1s;
+        const T f2 = T(0.125) * Bs * q2b * q2b + T(0.25) * Ds * e2s * e2s * e2s * e2s;
+        const T fp1 = T(0.5) * Bs * (T(1) + e1s) * q1 + Ds * e1s * e1s * e1s;
+        const T fp2 = T(0.5) * Bs * (T(1) + e2s) * q2b + Ds * e2s * e2s * e2s;
+        acc[0].add(T(0.5) * Cs * Wt * (dd1 * dd1 + dd2 * dd2));
+        acc[1].add(Wt * (f1 + f2));
         // dE/dF = F V diag(k) V^T with k_a = W (C (s_a - s*_a) + f'(s_a)) / s_a
         const T k1 = Wt * (Cs * dd1 + fp1) / s1;
         const T k2 = Wt * (Cs * dd2 + fp2) / s2;
-        noise += (double)(fabs(k1) * s1 * s1 + fabs(k2) * s2 * s2);
+        acc[5].add(fabs(k1) * s1 * s1 + fabs(k2) * s2 * s2);
         T vx, vy;
         if (rad == T(0)) {
             vx = T(1); vy = T(0);
@@ -228,7 +298,7 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
         dcr[0] = (E1[1] * d2[2] - E1[2] * d2[1]) + (d1[1] * E2[2] - d1[2] * E2[1]) + (d1[1] * d2[2] - d1[2] * d2[1]);
         dcr[1] = (E1[2] * d2[0] - E1[0] * d2[2]) + (d1[2] * E2[0] - d1[0] * E2[2]) + (d1[2] * d2[0] - d1[0] * d2[2]);
         dcr[2] = (E1[0] * d2[1] - E1[1] * d2[0]) + (d1[0] * E2[1] - d1[1] * E2[0]) + (d1[0] * d2[1] - d1[1] * d2[0]);
-        dV += (double)((Xi[0] * dcr[0] + Xi[1] * dcr[1] + Xi[2] * dcr[2]) + (Ui[0] * cr[0] + Ui[1] * cr[1] + Ui[2] * cr[2]));
+        acc[3].add((Xi[0] * dcr[0] + Xi[1] * dcr[1] + Xi[2] * dcr[2]) + (Ui[0] * cr[0] + Ui[1] * cr[1] + Ui[2] * cr[2]));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T G0 = F0[c] * K00 + F1[c] * K01;
@@ -247,7 +317,6 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
     __syncthreads();
 
     // bending per vertex (Eq. BendingDiscretizedPotential) and |grad C|^2
-    double eB = 0.0, gc2 = 0.0;
     for (int i = tid; i < n; i += NT) {
         const int b = __ldg(&tp.ring_ptr[i]), e = __ldg(&tp.ring_ptr[i + 1]);
         T dfn[3] = {T(0), T(0), T(0)}, dfu[3] = {T(0), T(0), T(0)};
@@ -266,7 +335,7 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
                 dfu[c] += cq * (U[c * np + jn] - Ui[c]);
             }
         }
-        T df[3] = {dfn[0] + dfu[0], dfn[1] + dfu[1], dfn[2] + dfu[2]};
+        const T df[3] = {dfn[0] + dfu[0], dfn[1] + dfu[1], dfn[2] + dfu[2]};
         const T nf = sqrt(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
         const T ng = __ldg(&tp.dg_norm[i]);
         T r[3];
@@ -276,7 +345,7 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
             for (int c = 0; c < 3; ++c) r[c] = df[c] * sc;
         } else if (ng > T(0)) {
             // delta_f ~ 0: the rotation is free; take the current vertex normal
-            T gcv[3] = {GC[i], GC[np + i], GC[2 * np + i]};
+            const T gcv[3] = {GC[i], GC[np + i], GC[2 * np + i]};
             const T gn = sqrt(gcv[0] * gcv[0] + gcv[1] * gcv[1] + gcv[2] * gcv[2]);
             const T s = gn > T(0) ? __ldg(&tp.nsign[i]) * ng / gn : T(0);
 #pragma unroll
@@ -287,8 +356,8 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
         }
         const T w = __ldg(&tp.bend_w[i]);
         const T rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        eB += (double)(T(0.5) * w * rr);
-        noise += (double)(w * sqrt(rr) * nf);
+        acc[2].add(T(0.5) * w * rr);
+        acc[5].add(w * sqrt(rr) * nf);
         for (int q = b; q < e; ++q) {
             const int jn = __ldg(&tp.ring_idx[q]);
             const T wc = w * __ldg(&tp.ring_c[q]);
@@ -298,45 +367,47 @@ __device__ EvalOut<T> evaluate(const TopoDev<T>& tp, const T* XN, const T* U, co
         const T wcs = w * __ldg(&tp.csum[i]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) atomicAdd(&Gout[c * np + i], -wcs * r[c]);
-        gc2 += (double)(GC[i] * GC[i] + GC[np + i] * GC[np + i] + GC[2 * np + i] * GC[2 * np + i]);
+        acc[4].add(GC[i] * GC[i] + GC[np + i] * GC[np + i] + GC[2 * np + i] * GC[2 * np + i]);
     }
-    double s7[7] = {eA, eS, eB, dV, gc2, noise, (double)bad};
-    block_sum<7>(s7, red);
-
-    EvalOut<T> o;
-    o.Earea = s7[0];
-    o.Esk = s7[1];
-    o.Ebend = s7[2];
-    o.V = Vn + s7[3] / 6.0;
-    const double Cv = o.V - tp.V0;
-    o.Evol = 0.5 * (double)tp.kvol * Cv * Cv / s7[4];
-    o.bad = s7[6] != 0.0;
-    const T volc = (T)((double)tp.kvol * Cv / s7[4]);
+    const double kvol = (double)tp.kvol, V0 = tp.V0;
+    block_reduce<T, 7>(acc, smem, [=](CellShared* s) {
+        s->Earea = s->out[0];
+        s->Esk = s->out[1];
+        s->Ebend = s->out[2];
+        s->V = Vn + s->out[3] / 6.0;
+        const double Cv = s->V - V0;
+        s->Evol = 0.5 * kvol * Cv * Cv / s->out[4];
+        s->volc = kvol * Cv / s->out[4];
+        s->noise = s->out[5];
+        s->bad = s->out[6] != 0.0;
+    });
+    const T volc = (T)sh->volc;
 
     // inertia (M~ = (1 + h alpha_D) M, diagonal), volume gradient, residual
     const T ms = tp.inertia_scale * tp.inv_h2, h2 = tp.h * tp.h;
-    double eI = 0.0, res2 = 0.0;
+    Acc<T> acc2[2];  // inertia energy, sum_i (h^2 |grad_i| / m_i)^2
     for (int i = tid; i < n; i += NT) {
         const T m = __ldg(&tp.mass[i]);
         const T hm = h2 * __ldg(&tp.inv_mass[i]);
-        T g2 = T(0);
+        T g2 = T(0), ei = T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T du = U[c * np + i] - UY[c * np + i];
             const T gv = Gout[c * np + i] + volc * GC[c * np + i] + m * ms * du;
             Gout[c * np + i] = gv;
-            eI += (double)(T(0.5) * m * ms * du * du);
+            ei += T(0.5) * m * ms * du * du;
             g2 += gv * gv;
         }
-        res2 += (double)(hm * hm * g2);
+        acc2[0].add(ei);
+        acc2[1].add(hm * hm * g2);
     }
-    double s2[2] = {eI, res2};
-    block_sum<2>(s2, red);
-    o.Ein = s2[0];
-    o.E = o.Ein + o.Earea + o.Esk + o.Ebend + o.Evol;
-    o.res = sqrt(s2[1] / (double)n) * (double)tp.inv_lbar;
-    o.noise = 4.0 * Unit<T>::u * (s7[5] + 2.0 * o.Ein);
-    return o;
+    const double inv_n = 1.0 / (double)n, inv_lbar = (double)tp.inv_lbar, uT = Unit<T>::u;
+    block_reduce<T, 2>(acc2, smem, [=](CellShared* s) {
+        s->Ein = s->out[0];
+        s->E = s->Ein + s->Earea + s->Esk + s->Ebend + s->Evol;
+        s->res = sqrt(s->out[1] * inv_n) * inv_lbar;
+        s->noise = 4.0 * uT * (s->noise + 2.0 * s->Ein);
+    });
 }
 
 // R = A^-1 Q for the three coordinate rows (A symmetric: column access is
@@ -349,30 +420,47 @@ __device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R)
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ntile = (n + 31) >> 5;
-    int nsplit = 1;
+    int nsplit = 8;
     for (int s = 1; s <= 8; ++s) {
-        int items = ntile * s, rounds = (items + nw - 1) / nw;
-        if (items * 10 >= rounds * nw * 9) { nsplit = s; break; }
-        nsplit = s;
+        const int items = ntile * s, rounds = (items + nw - 1) / nw;
+        if (items * 10 >= rounds * nw * 9) {
+            nsplit = s;
+            break;
+        }
     }
-    const int chunk = (n + nsplit - 1) / nsplit;
+    const int chunk = (((n + nsplit - 1) / nsplit) + 3) & ~3;  // multiple of 4: aligned vector loads of Q
     const T* __restrict__ A = tp.ainv;
     for (int item = warp; item < ntile * nsplit; item += nw) {
         const int rt = item / nsplit, js = item - rt * nsplit;
         const int row = rt * 32 + lane;
         const int j0 = js * chunk, j1 = min(n, j0 + chunk);
         T a0 = T(0), a1 = T(0), a2 = T(0);
-        if (row < n) {
+        if (row < n && j0 < j1) {
             int j = j0;
             for (; j + 4 <= j1; j += 4) {
-                T av[4];
+                T av[4], q0[4], q1[4], q2[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) av[u] = __ldg(&A[(size_t)(j + u) * np + row]);
+                if constexpr (sizeof(T) == 4) {
+                    const float4 x0 = *reinterpret_cast<const float4*>(Q + j);
+                    const float4 x1 = *reinterpret_cast<const float4*>(Q + np + j);
+                    const float4 x2 = *reinterpret_cast<const float4*>(Q + 2 * np + j);
+                    q0[0] = x0.x; q0[1] = x0.y; q0[2] = x0.z; q0[3] = x0.w;
+                    q1[0] = x1.x; q1[1] = x1.y; q1[2] = x1.z; q1[3] = x1.w;
+                    q2[0] = x2.x; q2[1] = x2.y; q2[2] = x2.z; q2[3] = x2.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        q0[u] = Q[j + u];
+                        q1[u] = Q[np + j + u];
+                        q2[u] = Q[2 * np + j + u];
+                    }
+                }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    a0 += av[u] * Q[j + u];
-                    a1 += av[u] * Q[np + j + u];
-                    a2 += av[u] * Q[2 * np + j + u];
+                    a0 += av[u] * q0[u];
+                    a1 += av[u] * q1[u];
+                    a2 += av[u] * q2[u];
                 }
             }
             for (; j < j1; ++j) {
@@ -395,9 +483,7 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
 {
     const TopoDev<T>& tp = gd.topo;
     const int n = tp.n, np = tp.n_pad, N3 = 3 * np, tid = threadIdx.x, NT = blockDim.x;
-    double* red = reinterpret_cast<double*>(smem);            // 32 warps x 16 doubles
-    double* s_rho = reinterpret_cast<double*>(smem + 4096);   // [kMaxHistory]
-    double* s_alpha = s_rho + kMaxHistory;                    // [kMaxHistory]
+    CellShared* sh = cell_shared(smem);
     char* slot = a.scratch ? a.scratch + (long long)blockIdx.x * a.slot_bytes : nullptr;
 
     T* XN = vec_ptr(gd, smem, slot, V_XN);
@@ -438,9 +524,10 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
         }
     }
     __syncthreads();
-    const double Vn = volume_at_xn(tp, XN, red);
+    volume_at_xn(tp, XN, smem);
+    const double Vn = sh->V;
 
-    EvalOut<T> ev = evaluate(tp, XN, u, UYv, g, GCv, Vn, red);
+    evaluate(tp, XN, u, UYv, g, GCv, Vn, smem);
     int evals = 1, iters = 0, status = NPFEM_CELL_OK;
 
     if (eval_mode) {
@@ -450,8 +537,8 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
         }
         if (tid == 0) {
             double* P = a.parts + 8 * item;
-            P[0] = ev.Ein; P[1] = ev.Earea; P[2] = ev.Esk; P[3] = ev.Ebend; P[4] = ev.Evol;
-            P[5] = ev.V; P[6] = ev.E; P[7] = ev.res;
+            P[0] = sh->Ein; P[1] = sh->Earea; P[2] = sh->Esk; P[3] = sh->Ebend; P[4] = sh->Evol;
+            P[5] = sh->V; P[6] = sh->E; P[7] = sh->res;
         }
         __syncthreads();
         return;
@@ -459,84 +546,90 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
 
     // ---- quasi-Newton iterations (L-BFGS, Nocedal & Wright Algorithm 7.4, H0 = H~^-1)
     int head = 0, count = 0;
-    double E = ev.E, noiseE = ev.noise, res = ev.res;
-    bool nonfinite = ev.bad || !isfinite(ev.E) || !isfinite(ev.res);
+    double E = sh->E, noiseE = sh->noise, res = sh->res, Vlast = sh->V;
+    bool nonfinite = sh->bad || !isfinite(sh->E) || !isfinite(sh->res);
+    const double c1 = a.p.c1, c2 = a.p.c2, anoise = a.p.armijo_noise;
     while (!nonfinite) {
         if (res <= a.p.tol) break;
-        if (iters >= a.p.max_iter) { status = NPFEM_CELL_MAXITER; break; }
+        if (iters >= a.p.max_iter) {
+            status = NPFEM_CELL_MAXITER;
+            break;
+        }
 
         // first loop: q = g; alpha_i = rho_i s_i^T q; q -= alpha_i y_i (newest first)
         for (int e = tid; e < N3; e += NT) Dv[e] = g[e];
-        __syncthreads();
         for (int q = 0; q < count; ++q) {
             const int i = (head - 1 - q + M) % M;
             const T* S = vec_ptr(gd, smem, slot, V_SBASE + i);
             const T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + i);
-            double d1[1] = {0.0};
-            T acc = T(0);
-            for (int e = tid; e < N3; e += NT) acc += S[e] * Dv[e];
-            d1[0] = (double)acc;
-            block_sum<1>(d1, red);
-            const double al = s_rho[i] * d1[0];
-            if (tid == 0) s_alpha[i] = al;
-            for (int e = tid; e < N3; e += NT) Dv[e] -= (T)al * Y[e];
-            __syncthreads();
+            Acc<T> acc[1];
+            T s = T(0);
+            for (int e = tid; e < N3; e += NT) s += S[e] * Dv[e];
+            acc[0].add(s);
+            block_reduce<T, 1>(acc, smem, [=](CellShared* c) { c->alpha[i] = c->rho[i] * c->out[0]; });
+            const T al = (T)sh->alpha[i];
+            for (int e = tid; e < N3; e += NT) Dv[e] -= al * Y[e];
         }
-        // r = H0 q through the dense inverse
+        // r = H0 q through the dense inverse (contract_simt syncs before reading q)
         contract_simt(tp, Dv, GCv);
         // second loop: beta = rho_i y_i^T r; r += s_i (alpha_i - beta) (oldest first)
         for (int q = count - 1; q >= 0; --q) {
             const int i = (head - 1 - q + M) % M;
             const T* S = vec_ptr(gd, smem, slot, V_SBASE + i);
             const T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + i);
-            T acc = T(0);
-            for (int e = tid; e < N3; e += NT) acc += Y[e] * GCv[e];
-            double d1[1] = {(double)acc};
-            block_sum<1>(d1, red);
-            const double be = s_rho[i] * d1[0];
-            const T coef = (T)(s_alpha[i] - be);
+            Acc<T> acc[1];
+            T s = T(0);
+            for (int e = tid; e < N3; e += NT) s += Y[e] * GCv[e];
+            acc[0].add(s);
+            block_reduce<T, 1>(acc, smem, [=](CellShared* c) { c->out[1] = c->alpha[i] - c->rho[i] * c->out[0]; });
+            const T coef = (T)sh->out[1];
             for (int e = tid; e < N3; e += NT) GCv[e] += S[e] * coef;
-            __syncthreads();
         }
-        double gd1[1];
+        double gdv;
         {
-            T acc = T(0);
+            Acc<T> acc[1];
+            T s = T(0);
             for (int e = tid; e < N3; e += NT) {
                 const T dv = -GCv[e];
                 Dv[e] = dv;
-                acc += g[e] * dv;
+                s += g[e] * dv;
             }
-            gd1[0] = (double)acc;
-            block_sum<1>(gd1, red);
+            acc[0].add(s);
+            block_reduce<T, 1>(acc, smem);
+            gdv = sh->out[0];
         }
-        double gdv = gd1[0];
         if (!(gdv < 0.0)) {
             // not a descent direction: drop the history, d = -H~^-1 g
             count = 0;
             contract_simt(tp, g, GCv);
-            T acc = T(0);
+            Acc<T> acc[1];
+            T s = T(0);
             for (int e = tid; e < N3; e += NT) {
                 const T dv = -GCv[e];
                 Dv[e] = dv;
-                acc += g[e] * dv;
+                s += g[e] * dv;
             }
-            double t1[1] = {(double)acc};
-            block_sum<1>(t1, red);
-            gdv = t1[0];
+            acc[0].add(s);
+            block_reduce<T, 1>(acc, smem);
+            gdv = sh->out[0];
         }
 
-        // backtracking line search alpha = 1, 1/2, ... (Armijo)
+        // backtracking line search alpha = 1, 1/2, ... (Armijo; the FP32 path widens the
+        // bound by a multiple of the estimated rounding error of g)
         double alpha = 1.0;
         bool accepted = false;
-        EvalOut<T> et;
         for (int hv = 0; hv <= a.p.max_halvings; ++hv) {
             const T al = (T)alpha;
             for (int e = tid; e < N3; e += NT) ut[e] = u[e] + al * Dv[e];
             __syncthreads();
-            et = evaluate(tp, XN, ut, UYv, gt, GCv, Vn, red);
+            evaluate(tp, XN, ut, UYv, gt, GCv, Vn, smem);
             ++evals;
-            if (a.p.fixed_alpha ||
-                (!et.bad && et.E <= E + a.p.c1 * alpha * gdv + a.p.armijo_noise * (et.noise + noiseE))) {
+            if (tid == 0) {
+                const bool ok = !sh->bad && sh->E <= E + c1 * alpha * gdv + anoise * (sh->noise + noiseE);
+                sh->accept = a.p.fixed_alpha || ok;
+            }
+            __syncthreads();
+            if (sh->accept) {
                 accepted = true;
                 break;
             }
@@ -549,6 +642,7 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
         // history pair (s, y) = (x_{k+1} - x_k, grad_{k+1} - grad_k), kept when the
         // curvature condition holds and s^T y > 0
         if (M > 0) {
+            Acc<T> acc[4];
             T sy = T(0), ss = T(0), yy = T(0), gtd = T(0);
             for (int e = tid; e < N3; e += NT) {
                 const T se = ut[e] - u[e], ye = gt[e] - g[e];
@@ -557,103 +651,116 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
                 yy += ye * ye;
                 gtd += gt[e] * Dv[e];
             }
-            double s4[4] = {(double)sy, (double)ss, (double)yy, (double)gtd};
-            block_sum<4>(s4, red);
-            if (s4[3] >= a.p.c2 * gdv && s4[0] > 1e-12 * sqrt(s4[1] * s4[2])) {
+            acc[0].add(sy);
+            acc[1].add(ss);
+            acc[2].add(yy);
+            acc[3].add(gtd);
+            const int hd = head;
+            block_reduce<T, 4>(acc, smem, [=](CellShared* c) {
+                c->push = c->out[3] >= c2 * gdv && c->out[0] > 1e-12 * sqrt(c->out[1] * c->out[2]);
+                if (c->push) c->rho[hd] = 1.0 / c->out[0];
+            });
+            if (sh->push) {
                 T* S = vec_ptr(gd, smem, slot, V_SBASE + head);
                 T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + head);
                 for (int e = tid; e < N3; e += NT) {
                     S[e] = ut[e] - u[e];
                     Y[e] = gt[e] - g[e];
                 }
-                if (tid == 0) s_rho[head] = 1.0 / s4[0];
                 head = (head + 1) % M;
                 count = count < M ? count + 1 : M;
-                __syncthreads();
             }
         }
         T* tp1 = u; u = ut; ut = tp1;
         T* tp2 = g; g = gt; gt = tp2;
-        E = et.E;
-        noiseE = et.noise;
-        res = et.res;
-        ev = et;
+        E = sh->E;
+        noiseE = sh->noise;
+        res = sh->res;
+        Vlast = sh->V;
         ++iters;
-        nonfinite = et.bad || !isfinite(et.E) || !isfinite(et.res);
+        nonfinite = sh->bad || !isfinite(sh->E) || !isfinite(sh->res);
+        __syncthreads();
     }
     if (nonfinite) status = NPFEM_CELL_NONFINITE;
 
     // ---- v_{n+1} = (x_{n+1} - x_n)/h and post-convergence dissipation (Sec. 2.1.4)
     const T inv_h = T(1) / h;
-    double sums[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) sums[q] = 0.0;
+    Acc<T> ps[16];
     if (!nonfinite) {
         for (int i = tid; i < n; i += NT) {
-            const double m = (double)__ldg(&tp.mass[i]);
-            double xr[3], vr[3];
+            const T m = __ldg(&tp.mass[i]);
+            T xr[3], vr[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                xr[c] = (double)XN[c * np + i] + (double)u[c * np + i];
-                vr[c] = (double)(u[c * np + i] * inv_h);
+                xr[c] = XN[c * np + i] + u[c * np + i];
+                vr[c] = u[c * np + i] * inv_h;
             }
-            sums[0] += m;
+            ps[0].add(m);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                sums[1 + c] += m * xr[c];
-                sums[4 + c] += m * vr[c];
+                ps[1 + c].add(m * xr[c]);
+                ps[4 + c].add(m * vr[c]);
             }
-            sums[7] += m * (xr[1] * vr[2] - xr[2] * vr[1]);
-            sums[8] += m * (xr[2] * vr[0] - xr[0] * vr[2]);
-            sums[9] += m * (xr[0] * vr[1] - xr[1] * vr[0]);
-            sums[10] += m * xr[0] * xr[0];
-            sums[11] += m * xr[1] * xr[1];
-            sums[12] += m * xr[2] * xr[2];
-            sums[13] += m * xr[0] * xr[1];
-            sums[14] += m * xr[0] * xr[2];
-            sums[15] += m * xr[1] * xr[2];
+            ps[7].add(m * (xr[1] * vr[2] - xr[2] * vr[1]));
+            ps[8].add(m * (xr[2] * vr[0] - xr[0] * vr[2]));
+            ps[9].add(m * (xr[0] * vr[1] - xr[1] * vr[0]));
+            ps[10].add(m * xr[0] * xr[0]);
+            ps[11].add(m * xr[1] * xr[1]);
+            ps[12].add(m * xr[2] * xr[2]);
+            ps[13].add(m * xr[0] * xr[1]);
+            ps[14].add(m * xr[0] * xr[2]);
+            ps[15].add(m * xr[1] * xr[2]);
         }
     }
-    block_sum<16>(sums, red);
-    double w[3] = {0.0, 0.0, 0.0}, xc[3] = {0, 0, 0}, vc[3] = {0, 0, 0};
-    if (!nonfinite) {
-        const double Mt = sums[0];
+    const bool nf = nonfinite;
+    block_reduce<T, 16>(ps, smem, [=](CellShared* s) {
+        double* o = s->out;
+        double* P = s->post;
+        for (int q = 0; q < 9; ++q) P[q] = 0.0;
+        if (nf) return;
+        const double Mt = o[0];
+        double xc[3], vc[3];
         for (int c = 0; c < 3; ++c) {
-            xc[c] = sums[1 + c] / Mt;
-            vc[c] = sums[4 + c] / Mt;
+            xc[c] = o[1 + c] / Mt;
+            vc[c] = o[4 + c] / Mt;
         }
         // angular momentum and inertia tensor about the centre of mass
-        const double L0 = sums[7] - Mt * (xc[1] * vc[2] - xc[2] * vc[1]);
-        const double L1 = sums[8] - Mt * (xc[2] * vc[0] - xc[0] * vc[2]);
-        const double L2 = sums[9] - Mt * (xc[0] * vc[1] - xc[1] * vc[0]);
-        const double Sxx = sums[10] - Mt * xc[0] * xc[0], Syy = sums[11] - Mt * xc[1] * xc[1],
-                     Szz = sums[12] - Mt * xc[2] * xc[2];
-        const double Sxy = sums[13] - Mt * xc[0] * xc[1], Sxz = sums[14] - Mt * xc[0] * xc[2],
-                     Syz = sums[15] - Mt * xc[1] * xc[2];
+        const double L0 = o[7] - Mt * (xc[1] * vc[2] - xc[2] * vc[1]);
+        const double L1 = o[8] - Mt * (xc[2] * vc[0] - xc[0] * vc[2]);
+        const double L2 = o[9] - Mt * (xc[0] * vc[1] - xc[1] * vc[0]);
+        const double Sxx = o[10] - Mt * xc[0] * xc[0], Syy = o[11] - Mt * xc[1] * xc[1], Szz = o[12] - Mt * xc[2] * xc[2];
+        const double Sxy = o[13] - Mt * xc[0] * xc[1], Sxz = o[14] - Mt * xc[0] * xc[2], Syz = o[15] - Mt * xc[1] * xc[2];
         const double I00 = Syy + Szz, I11 = Sxx + Szz, I22 = Sxx + Syy;
         const double I01 = -Sxy, I02 = -Sxz, I12 = -Syz;
         const double c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
         const double c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
         const double det = I00 * c00 + I01 * c01 + I02 * c02;
-        w[0] = (c00 * L0 + c01 * L1 + c02 * L2) / det;
-        w[1] = (c01 * L0 + c11 * L1 + c12 * L2) / det;
-        w[2] = (c02 * L0 + c12 * L1 + c22 * L2) / det;
-    }
-    const double kap = (double)tp.kappa;
+        for (int c = 0; c < 3; ++c) {
+            P[c] = xc[c];
+            P[3 + c] = vc[c];
+        }
+        P[6] = (c00 * L0 + c01 * L1 + c02 * L2) / det;
+        P[7] = (c01 * L0 + c11 * L1 + c12 * L2) / det;
+        P[8] = (c02 * L0 + c12 * L1 + c22 * L2) / det;
+    });
+    const T xc[3] = {(T)sh->post[0], (T)sh->post[1], (T)sh->post[2]};
+    const T vc[3] = {(T)sh->post[3], (T)sh->post[4], (T)sh->post[5]};
+    const T w[3] = {(T)sh->post[6], (T)sh->post[7], (T)sh->post[8]};
+    const T kap = tp.kappa;
+    T* x = a.x + so;
+    T* v = a.v + so;
     for (int i = tid; i < n; i += NT) {
-        T* x = a.x + so;
-        T* v = a.v + so;
         if (nonfinite) {
             for (int c = 0; c < 3; ++c) v[c * n + i] = T(0);
             continue;
         }
-        double r[3];
-        for (int c = 0; c < 3; ++c) r[c] = (double)XN[c * np + i] + (double)u[c * np + i] - xc[c];
-        const double wr[3] = {w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2], w[0] * r[1] - w[1] * r[0]};
+        T r[3];
+        for (int c = 0; c < 3; ++c) r[c] = XN[c * np + i] + u[c * np + i] - xc[c];
+        const T wr[3] = {w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2], w[0] * r[1] - w[1] * r[0]};
         for (int c = 0; c < 3; ++c) {
             const T uc = u[c * np + i];
-            const double vv = (double)(uc * inv_h);
-            v[c * n + i] = (T)(vv + kap * (vc[c] + wr[c] - vv));
+            const T vv = uc * inv_h;
+            v[c * n + i] = vv + kap * (vc[c] + wr[c] - vv);
             x[c * n + i] = x[c * n + i] + uc;
         }
     }
@@ -664,7 +771,7 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
         st.status = status;
         st.residual = (float)res;
         st.objective = E;
-        st.volume = ev.V;
+        st.volume = Vlast;
         a.stats[item] = st;
     }
     __syncthreads();
