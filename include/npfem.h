@@ -149,6 +149,26 @@ int npfem_destroy(npfem_handle* h);
 int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
                const void* f_ext, double dt, void* stream, npfem_cell_stats* stats);
 
+/* Allocation-free npfem_step.  The paper has no counterpart: this entry point
+   exists for callers that cannot allocate device memory when they step -- a host
+   program whose caching allocator has reserved the GPU (so a raw cudaMalloc from
+   this library may fail), or a time loop that cannot afford the device-wide
+   synchronisation of cudaMalloc/cudaFree.  npfem_step may grow a library-owned
+   scratch buffer the first time a mesh needs one; npfem_step_static never
+   allocates: its scratch (per-block vector slots for meshes whose solver vectors do
+   not fit in shared memory, plus the work counters) is a fixed 32 MiB __device__
+   array compiled into the library, held by every GPU that loads the library until
+   the process exits.  Arguments, layout, results and errors are those of
+   npfem_step (same kernel; with large meshes it may run fewer persistent blocks so
+   that their slots fit), plus INVALID_ARG when one block's scratch exceeds the
+   array.  The first call on a device looks up the array's device address (a host
+   reference to it is not a device pointer); make that first call before any
+   stream capture.  All calls on a device share the array and it keeps the last
+   call's contents (the work counters are cleared on `stream` before each launch):
+   calls whose kernels overlap on the GPU race and must be avoided. */
+int npfem_step_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
+                      const void* f_ext, double dt, void* stream, npfem_cell_stats* stats);
+
 /* Same as npfem_step for one handle with HOST buffers: copies x, v, f_ext (host,
    SoA, same element type) to library-owned device buffers, steps, and copies x, v
    and (if stats_host != NULL) the per-cell stats back; returns after the copies

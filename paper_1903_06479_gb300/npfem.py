@@ -47,7 +47,7 @@ CELL_STATS_DTYPE = np.dtype([("iterations", "<i4"), ("evaluations", "<i4"), ("st
 
 _lib = None
 EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", "npfem_step_host", "npfem_eval",
-           "npfem_get_inverse", "npfem_get_rest_info", "npfem_last_error")
+           "npfem_get_inverse", "npfem_get_rest_info", "npfem_last_error", "npfem_step_static")
 
 
 def lib_path() -> str:
@@ -66,6 +66,7 @@ def lib():
         L.npfem_create.argtypes = [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Opts), C.c_double, i32, C.POINTER(vp)]
         L.npfem_destroy.argtypes = [vp]
         L.npfem_step.argtypes = [C.POINTER(vp), i32, C.POINTER(C.c_int32), vp, vp, vp, C.c_double, vp, vp]
+        L.npfem_step_static.argtypes = [C.POINTER(vp), i32, C.POINTER(C.c_int32), vp, vp, vp, C.c_double, vp, vp]
         L.npfem_step_host.argtypes = [vp, i32, vp, vp, vp, C.c_double, vp, vp]
         L.npfem_eval.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.npfem_get_inverse.argtypes = [vp, vp]
@@ -175,3 +176,12 @@ def step(handles, cells_per_group, x, v, f, dt: float, stream=None, stats=None):
     cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
     _check(lib().npfem_step(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), _addr(stream),
                             _addr(stats)))
+
+
+def step_static(handles, cells_per_group, x, v, f, dt: float, stream=None, stats=None):
+    """npfem_step_static: npfem_step without any device allocation (fixed library scratch)."""
+    handles = list(handles)
+    arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
+    _check(lib().npfem_step_static(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), _addr(stream),
+                                   _addr(stats)))
