@@ -97,6 +97,10 @@ int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv)
     std::vector<unsigned short> ridx(H.ring_idx.begin(), H.ring_idx.end());
     if ((rc = upload(h, ridx, &tp->ring_idx))) return rc;
     if ((rc = upload(h, H.ring_c, &tp->ring_c))) return rc;
+    if ((rc = upload(h, H.ring_ct, &tp->ring_ct))) return rc;
+    if ((rc = upload(h, H.inc_ptr, &tp->inc_ptr))) return rc;
+    std::vector<unsigned> incu(H.inc_idx.begin(), H.inc_idx.end());
+    if ((rc = upload(h, incu, &tp->inc_idx))) return rc;
     tp->n = H.n;
     tp->nt = H.nt;
     tp->n_pad = h->n_pad;
@@ -152,7 +156,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
         g.state_off = state;
         g.cells = cells[gi];
         long long sb = 0;
-        place_vectors(&g, h->n_pad, h0->opts.lbfgs_m, budget, &sb);
+        place_vectors(&g, h->n_pad, h->nt, h0->opts.lbfgs_m, budget, &sb);
         slot = std::max(slot, sb);
         smem_max = std::max(smem_max, g.smem_bytes);
         total += cells[gi];

@@ -15,11 +15,13 @@ namespace npfem {
 
 constexpr int kMaxGroups = 8;     // meshes per npfem_step launch
 constexpr int kMaxHistory = 8;    // L-BFGS window limit
-constexpr int kNumBaseVecs = 8;   // XN U UT G GT GC UY D, then S[m], Y[m]
+constexpr int kNumBaseVecs = 10;  // XN U UT G GT GC UY D TRI WR, then S[m], Y[m]
 constexpr int kMaxVecs = kNumBaseVecs + 2 * kMaxHistory;
 constexpr int kFixedSmem = 12288; // reduction scratch (8 KB) + per-cell scalars at the start of dynamic smem
 
-enum Vec { V_XN = 0, V_U = 1, V_UT = 2, V_G = 3, V_GT = 4, V_GC = 5, V_UY = 6, V_D = 7, V_SBASE = 8 };
+// Per-cell buffers.  All are 3 x n_pad values except TRI (9 values per triangle:
+// the gradient contributions of corners j and k and the area-weighted normal / 6).
+enum Vec { V_XN = 0, V_U = 1, V_UT = 2, V_G = 3, V_GT = 4, V_GC = 5, V_UY = 6, V_D = 7, V_TRI = 8, V_WR = 9, V_SBASE = 10 };
 
 enum Contraction { CONTRACT_SIMT = 0, CONTRACT_TC_TF32 = 1, CONTRACT_TC_BF16 = 2 };
 
@@ -40,6 +42,9 @@ struct TopoDev {
     const int* ring_ptr;         // [n + 1]
     const unsigned short* ring_idx;  // [nnz]
     const T* ring_c;             // [nnz] cotangent weights / (2 A_i)
+    const T* ring_ct;            // [nnz] weight of vertex i in the ring of its neighbour j
+    const int* inc_ptr;          // [n + 1] vertex -> incident triangles
+    const unsigned* inc_idx;     // [3 nt] (triangle << 2) | corner
     const T* ainv;               // [n_pad][n_pad] A^-1 in T (zero padding)
     const void* ainv_lp;         // A^-1 for the tensor-core contraction (bf16 or tf32-rounded fp32)
     const int* h_ptr;            // sparse H~ (CSR, fp32) for the refinement sweep
@@ -94,7 +99,9 @@ struct HostTopo {
     std::vector<double> dminv, W;             // [nt][4], [nt]
     std::vector<double> mass, avor, bend_w, dg_norm, csum, nsign;  // [n]
     std::vector<int> ring_ptr, ring_idx;      // CSR one-ring
-    std::vector<double> ring_c;
+    std::vector<double> ring_c;               // c_ij for entry (i, j)
+    std::vector<double> ring_ct;              // c_ji for entry (i, j): weight of i in the ring of j
+    std::vector<int> inc_ptr, inc_idx;        // vertex -> incident (triangle << 2 | corner)
     std::vector<int> L_ptr, L_idx;            // CSR of L (full symmetric)
     std::vector<double> L_val;
     double V0 = 0, A0 = 0, lbar = 0, mtotal = 0;
@@ -120,14 +127,20 @@ cudaError_t set_cell_kernel_smem(int bytes);
 // Records msg as the calling thread's last error and returns code (npfem_api.cu).
 int set_error(int code, const std::string& msg);
 
-// Places the per-cell vectors: shared memory in priority order while it fits, the
-// rest in a per-block global slot.  Returns the smem bytes (after kFixedSmem).
+// Places the per-cell buffers: shared memory in priority order while they fit (the
+// randomly gathered ones first), the rest in a per-block global slot.  smem offsets
+// start at base_off.  Returns the smem bytes used in g->smem_bytes.
 template <typename T>
-inline void place_vectors(GroupDesc<T>* g, int n_pad, int m, int smem_budget, long long* slot_bytes)
+inline void place_vectors(GroupDesc<T>* g, int n_pad, int nt, int m, int smem_budget, long long* slot_bytes,
+                          int base_off = 0)
 {
     const int vb = 3 * n_pad * (int)sizeof(T);
+    // TRI also serves as the contraction's scratch: (max(32 warps, row tiles) x 384 floats)
+    const int tri_bytes = 9 * nt * (int)sizeof(T);
+    const int ctr_bytes = (((n_pad + 127) / 128) > 32 ? ((n_pad + 127) / 128) : 32) * 384 * 4;
+    const int tb = ((tri_bytes > ctr_bytes ? tri_bytes : ctr_bytes) + 15) & ~15;
     int order[kMaxVecs], nv = 0;
-    const int base[kNumBaseVecs] = {V_XN, V_U, V_UT, V_G, V_GT, V_GC, V_UY, V_D};
+    const int base[kNumBaseVecs] = {V_XN, V_U, V_UT, V_TRI, V_WR, V_G, V_GT, V_GC, V_UY, V_D};
     for (int q = 0; q < kNumBaseVecs; ++q) order[nv++] = base[q];
     for (int q = 0; q < m; ++q) {
         order[nv++] = V_SBASE + q;
@@ -137,15 +150,16 @@ inline void place_vectors(GroupDesc<T>* g, int n_pad, int m, int smem_budget, lo
     long long gl = 0;
     for (int q = 0; q < kMaxVecs; ++q) g->loc[q] = 0;
     for (int q = 0; q < nv; ++q) {
-        if (used + vb <= smem_budget) {
-            g->loc[order[q]] = used;
-            used += vb;
+        const int sz = order[q] == V_TRI ? tb : vb;
+        if (used + sz <= smem_budget) {
+            g->loc[order[q]] = base_off + used;
+            used += sz;
         } else {
             g->loc[order[q]] = -(int)gl - 1;
-            gl += vb;
+            gl += sz;
         }
     }
-    g->smem_bytes = used;
+    g->smem_bytes = base_off + used;
     *slot_bytes = gl;
 }
 

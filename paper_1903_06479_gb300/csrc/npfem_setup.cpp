@@ -198,6 +198,25 @@ int build_host_topo(const npfem_mesh* mesh, const npfem_material* mat, int equal
     }
     o->ring_ptr[n] = (int)o->ring_idx.size();
     o->lbar = lsum / (double)ecount;
+    // transposed weights: the bending gradient is gathered per vertex, which needs
+    // the weight each neighbour's ring gives to this vertex
+    o->ring_ct.assign(o->ring_idx.size(), 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int q = o->ring_ptr[i]; q < o->ring_ptr[i + 1]; ++q) {
+            const int j = o->ring_idx[q];
+            for (int p = o->ring_ptr[j]; p < o->ring_ptr[j + 1]; ++p)
+                if (o->ring_idx[p] == i) o->ring_ct[q] = o->ring_c[p];
+        }
+    // vertex -> (triangle, corner) incidence, for gathering per-triangle gradients
+    o->inc_ptr.assign(n + 1, 0);
+    for (int q = 0; q < 3 * nt; ++q) o->inc_ptr[mesh->tris[q] + 1]++;
+    for (int i = 0; i < n; ++i) o->inc_ptr[i + 1] += o->inc_ptr[i];
+    o->inc_idx.assign(3 * (size_t)nt, 0);
+    {
+        std::vector<int> fillp(o->inc_ptr.begin(), o->inc_ptr.end() - 1);
+        for (int t = 0; t < nt; ++t)
+            for (int a = 0; a < 3; ++a) o->inc_idx[fillp[mesh->tris[3 * t + a]]++] = (t << 2) | a;
+    }
 
     // --- lumped masses
     o->mtotal = mat->density * V0;

@@ -133,6 +133,105 @@ __device__ __forceinline__ void block_reduce(Acc<T> (&a)[K], unsigned char* smem
     __syncthreads();
 }
 
+// Like block_reduce, for KC compensated and KP plain sums (out[0..KC) compensated,
+// out[KC..KC+KP) plain).
+template <typename T, int KC, int KP, typename Epi = NoEpi>
+__device__ __forceinline__ void block_reduce_cp(Acc<T> (&a)[KC], T (&p)[KP], unsigned char* smem, Epi epi = Epi())
+{
+    constexpr int W = 2 * KC + KP;
+    T* red = reinterpret_cast<T*>(smem);  // [32 warps][W]
+    CellShared* sh = cell_shared(smem);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const T h2 = __shfl_xor_sync(kFull, a[k].hi, o);
+            const T l2 = __shfl_xor_sync(kFull, a[k].lo, o);
+            a[k].merge(h2, l2);
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) p[k] += __shfl_xor_sync(kFull, p[k], o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            red[w * W + 2 * k] = a[k].hi;
+            red[w * W + 2 * k + 1] = a[k].lo;
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) red[w * W + 2 * KC + k] = p[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+        Acc<T> b[KC];
+        T q[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) q[k] = T(0);
+        if (lane < nw) {
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                b[k].hi = red[lane * W + 2 * k];
+                b[k].lo = red[lane * W + 2 * k + 1];
+            }
+#pragma unroll
+            for (int k = 0; k < KP; ++k) q[k] = red[lane * W + 2 * KC + k];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const T h2 = __shfl_xor_sync(kFull, b[k].hi, o);
+                const T l2 = __shfl_xor_sync(kFull, b[k].lo, o);
+                b[k].merge(h2, l2);
+            }
+#pragma unroll
+            for (int k = 0; k < KP; ++k) q[k] += __shfl_xor_sync(kFull, q[k], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < KC; ++k) sh->out[k] = (double)b[k].hi + (double)b[k].lo;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) sh->out[KC + k] = (double)q[k];
+            epi(sh);
+        }
+    }
+    __syncthreads();
+}
+
+// Plain (uncompensated) block sum of K values, for dot products of the direction.
+template <typename T, int K, typename Epi = NoEpi>
+__device__ __forceinline__ void block_sum(T (&p)[K], unsigned char* smem, Epi epi = Epi())
+{
+    T* red = reinterpret_cast<T*>(smem);
+    CellShared* sh = cell_shared(smem);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k) p[k] += __shfl_xor_sync(kFull, p[k], o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[w * K + k] = p[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+        T q[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) q[k] = lane < nw ? red[lane * K + k] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < K; ++k) q[k] += __shfl_xor_sync(kFull, q[k], o);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) sh->out[k] = (double)q[k];
+            epi(sh);
+        }
+    }
+    __syncthreads();
+}
+
 // SL(2) projection of the principal stretches (Sec. 2.1.2, area preservation):
 // Sigma* = diag(a, 1/a) closest to diag(s1, s2), s1 >= s2.  With a = 1 + t,
 // s1 = 1 + e1, s2 = 1 + e2 the stationarity condition a^4 - s1 a^3 + s2 a - 1 = 0
@@ -198,21 +297,24 @@ __device__ void volume_at_xn(const TopoDev<T>& tp, const T* XN, unsigned char* s
 // projection), modified Skalak (first Piola-Kirchhoff forces).  Results are left in
 // cell_shared(smem): E, its parts, V, residual r, rounding estimate of E, bad flag.
 // Vn is the volume at x_n (held by the caller).
+//
+// Gather form, no atomics: pass 1 writes each triangle's corner gradients and
+// area-weighted normal to TRI; pass 2 gathers them per vertex (vertex -> triangle
+// incidence) and computes the bending residual w_i r_i into WR; pass 3 gathers the
+// bending gradient from the neighbours' WR (transposed cotangent weights) and adds
+// the volume and inertia terms.  Every vertex is written by one thread only.
 template <typename T>
-__device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T* UY, T* Gout, T* GC, double Vn,
-                         unsigned char* smem)
+__device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T* UY, T* Gout, T* GC, T* TRI, T* WR,
+                         double Vn, unsigned char* smem)
 {
-    const int n = tp.n, np = tp.n_pad, N3 = 3 * np, tid = threadIdx.x, NT = blockDim.x;
+    const int n = tp.n, np = tp.n_pad, tid = threadIdx.x, NT = blockDim.x;
     CellShared* sh = cell_shared(smem);
-    for (int e = tid; e < N3; e += NT) {
-        Gout[e] = T(0);
-        GC[e] = T(0);
-    }
-    __syncthreads();
-
     const T Cs = tp.C, Bs = tp.B, Ds = tp.Dsk;
     const T sixth = T(1) / T(6);
-    Acc<T> acc[7];  // area, skalak, bending, dV*6, |grad C|^2, noise, bad
+    Acc<T> ce[4];  // area, Skalak, bending energies; 6 dV
+    T pl[3] = {T(0), T(0), T(0)};  // |grad C|^2, rounding estimate, degenerate count
+
+    // ---- pass 1: triangles
     for (int t = tid; t < tp.nt; t += NT) {
         const ushort4 tv = __ldg(&tp.tri[t]);
         const int i = tv.x, j = tv.y, k = tv.z;
@@ -238,6 +340,7 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
             e1[c] = E1[c] + d1[c];
             e2[c] = E2[c] + d2[c];
         }
+        T* out = TRI + 9 * t;
         // F = D_s D_m^{-1} (3 x 2), columns F0, F1
         T F0[3], F1[3];
 #pragma unroll
@@ -256,8 +359,16 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
         const T s1 = sqrt(T(1) + m1);
         const T q2 = T(1) + m2;
         const T s2 = q2 > T(0) ? sqrt(q2) : T(0);
+        T cr[3];
+        cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
         if (!(s2 > T(1e-6) * s1) || !(s1 < T(1e30))) {
-            acc[6].add(T(1));
+            pl[2] += T(1);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) out[c] = T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[6 + c] = cr[c] * sixth;
             continue;
         }
         const T e1s = m1 / (s1 + T(1)), e2s = m2 / (s2 + T(1));
@@ -270,12 +381,12 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
         const T f2 = T(0.125) * Bs * q2b * q2b + T(0.25) * Ds * e2s * e2s * e2s * e2s;
         const T fp1 = T(0.5) * Bs * (T(1) + e1s) * q1 + Ds * e1s * e1s * e1s;
         const T fp2 = T(0.5) * Bs * (T(1) + e2s) * q2b + Ds * e2s * e2s * e2s;
-        acc[0].add(T(0.5) * Cs * Wt * (dd1 * dd1 + dd2 * dd2));
-        acc[1].add(Wt * (f1 + f2));
+        ce[0].add(T(0.5) * Cs * Wt * (dd1 * dd1 + dd2 * dd2));
+        ce[1].add(Wt * (f1 + f2));
         // dE/dF = F V diag(k) V^T with k_a = W (C (s_a - s*_a) + f'(s_a)) / s_a
         const T k1 = Wt * (Cs * dd1 + fp1) / s1;
         const T k2 = Wt * (Cs * dd2 + fp2) / s2;
-        acc[5].add(fabs(k1) * s1 * s1 + fabs(k2) * s2 * s2);
+        pl[1] += fabs(k1) * s1 * s1 + fabs(k2) * s2 * s2;
         T vx, vy;
         if (rad == T(0)) {
             vx = T(1); vy = T(0);
@@ -290,35 +401,55 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
         const T K00 = k1 * vx * vx + k2 * vy * vy;
         const T K11 = k1 * vy * vy + k2 * vx * vx;
         const T K01 = (k1 - k2) * vx * vy;
-        T cr[3], dcr[3];
-        cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
-        cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
-        cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
         // cross-product change relative to x_n: E1 x d2 + d1 x E2 + d1 x d2
+        T dcr[3];
         dcr[0] = (E1[1] * d2[2] - E1[2] * d2[1]) + (d1[1] * E2[2] - d1[2] * E2[1]) + (d1[1] * d2[2] - d1[2] * d2[1]);
         dcr[1] = (E1[2] * d2[0] - E1[0] * d2[2]) + (d1[2] * E2[0] - d1[0] * E2[2]) + (d1[2] * d2[0] - d1[0] * d2[2]);
         dcr[2] = (E1[0] * d2[1] - E1[1] * d2[0]) + (d1[0] * E2[1] - d1[1] * E2[0]) + (d1[0] * d2[1] - d1[1] * d2[0]);
-        acc[3].add((Xi[0] * dcr[0] + Xi[1] * dcr[1] + Xi[2] * dcr[2]) + (Ui[0] * cr[0] + Ui[1] * cr[1] + Ui[2] * cr[2]));
+        ce[3].add((Xi[0] * dcr[0] + Xi[1] * dcr[1] + Xi[2] * dcr[2]) + (Ui[0] * cr[0] + Ui[1] * cr[1] + Ui[2] * cr[2]));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T G0 = F0[c] * K00 + F1[c] * K01;
             const T G1 = F0[c] * K01 + F1[c] * K11;
-            const T gj = G0 * Di0 + G1 * Di1;
-            const T gk = G0 * Di2 + G1 * Di3;
-            atomicAdd(&Gout[c * np + j], gj);
-            atomicAdd(&Gout[c * np + k], gk);
-            atomicAdd(&Gout[c * np + i], -(gj + gk));
-            const T g6 = cr[c] * sixth;
-            atomicAdd(&GC[c * np + i], g6);
-            atomicAdd(&GC[c * np + j], g6);
-            atomicAdd(&GC[c * np + k], g6);
+            out[c] = G0 * Di0 + G1 * Di1;      // corner j
+            out[3 + c] = G0 * Di2 + G1 * Di3;  // corner k (corner i gets minus both)
+            out[6 + c] = cr[c] * sixth;        // share of the area-weighted normal / 3
         }
     }
     __syncthreads();
 
-    // bending per vertex (Eq. BendingDiscretizedPotential) and |grad C|^2
-    for (int i = tid; i < n; i += NT) {
-        const int b = __ldg(&tp.ring_ptr[i]), e = __ldg(&tp.ring_ptr[i + 1]);
+    // ---- pass 2: gather per vertex; bending projection (Eq. BendingDiscretizedPotential)
+    for (int i = tid; i < np; i += NT) {
+        if (i >= n) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Gout[c * np + i] = T(0);
+                GC[c * np + i] = T(0);
+                WR[c * np + i] = T(0);
+            }
+            continue;
+        }
+        T g[3] = {T(0), T(0), T(0)}, gc[3] = {T(0), T(0), T(0)};
+        const int b0 = __ldg(&tp.inc_ptr[i]), b1 = __ldg(&tp.inc_ptr[i + 1]);
+        for (int q = b0; q < b1; ++q) {
+            const unsigned e = __ldg(&tp.inc_idx[q]);
+            const T* P = TRI + 9 * (e >> 2);
+            const unsigned corner = e & 3u;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T gj = P[c], gk = P[3 + c];
+                g[c] += corner == 1u ? gj : (corner == 2u ? gk : -(gj + gk));
+                gc[c] += P[6 + c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Gout[c * np + i] = g[c];
+            GC[c * np + i] = gc[c];
+        }
+        pl[0] += gc[0] * gc[0] + gc[1] * gc[1] + gc[2] * gc[2];
+
+        const int r0 = __ldg(&tp.ring_ptr[i]), r1 = __ldg(&tp.ring_ptr[i + 1]);
         T dfn[3] = {T(0), T(0), T(0)}, dfu[3] = {T(0), T(0), T(0)};
         T Xi[3], Ui[3];
 #pragma unroll
@@ -326,7 +457,7 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
             Xi[c] = XN[c * np + i];
             Ui[c] = U[c * np + i];
         }
-        for (int q = b; q < e; ++q) {
+        for (int q = r0; q < r1; ++q) {
             const int jn = __ldg(&tp.ring_idx[q]);
             const T cq = __ldg(&tp.ring_c[q]);
 #pragma unroll
@@ -345,136 +476,181 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
             for (int c = 0; c < 3; ++c) r[c] = df[c] * sc;
         } else if (ng > T(0)) {
             // delta_f ~ 0: the rotation is free; take the current vertex normal
-            const T gcv[3] = {GC[i], GC[np + i], GC[2 * np + i]};
-            const T gn = sqrt(gcv[0] * gcv[0] + gcv[1] * gcv[1] + gcv[2] * gcv[2]);
+            const T gn = sqrt(gc[0] * gc[0] + gc[1] * gc[1] + gc[2] * gc[2]);
             const T s = gn > T(0) ? __ldg(&tp.nsign[i]) * ng / gn : T(0);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r[c] = df[c] - s * gcv[c];
+            for (int c = 0; c < 3; ++c) r[c] = df[c] - s * gc[c];
         } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) r[c] = df[c];
         }
         const T w = __ldg(&tp.bend_w[i]);
         const T rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        acc[2].add(T(0.5) * w * rr);
-        acc[5].add(w * sqrt(rr) * nf);
-        for (int q = b; q < e; ++q) {
-            const int jn = __ldg(&tp.ring_idx[q]);
-            const T wc = w * __ldg(&tp.ring_c[q]);
+        ce[2].add(T(0.5) * w * rr);
+        pl[1] += w * sqrt(rr) * nf;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(&Gout[c * np + jn], wc * r[c]);
-        }
-        const T wcs = w * __ldg(&tp.csum[i]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) atomicAdd(&Gout[c * np + i], -wcs * r[c]);
-        acc[4].add(GC[i] * GC[i] + GC[np + i] * GC[np + i] + GC[2 * np + i] * GC[2 * np + i]);
+        for (int c = 0; c < 3; ++c) WR[c * np + i] = w * r[c];
     }
     const double kvol = (double)tp.kvol, V0 = tp.V0;
-    block_reduce<T, 7>(acc, smem, [=](CellShared* s) {
+    block_reduce_cp<T, 4, 3>(ce, pl, smem, [=](CellShared* s) {
         s->Earea = s->out[0];
         s->Esk = s->out[1];
         s->Ebend = s->out[2];
         s->V = Vn + s->out[3] / 6.0;
         const double Cv = s->V - V0;
-        s->Evol = 0.5 * kvol * Cv * Cv / s->out[4];
-        s->volc = kvol * Cv / s->out[4];
+        const T inv = T(1) / (T)s->out[4];
+        s->Evol = 0.5 * kvol * Cv * Cv * (double)inv;
+        s->volc = kvol * Cv * (double)inv;
         s->noise = s->out[5];
         s->bad = s->out[6] != 0.0;
     });
     const T volc = (T)sh->volc;
 
-    // inertia (M~ = (1 + h alpha_D) M, diagonal), volume gradient, residual
+    // ---- pass 3: bending gather, volume and inertia (M~ = (1 + h alpha_D) M), residual
     const T ms = tp.inertia_scale * tp.inv_h2, h2 = tp.h * tp.h;
-    Acc<T> acc2[2];  // inertia energy, sum_i (h^2 |grad_i| / m_i)^2
+    Acc<T> ci[1];            // inertia energy
+    T pr[1] = {T(0)};        // sum_i (h^2 |grad_i| / m_i)^2
     for (int i = tid; i < n; i += NT) {
         const T m = __ldg(&tp.mass[i]);
         const T hm = h2 * __ldg(&tp.inv_mass[i]);
+        const int r0 = __ldg(&tp.ring_ptr[i]), r1 = __ldg(&tp.ring_ptr[i + 1]);
+        const T cs = __ldg(&tp.csum[i]);
+        T gb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gb[c] = -cs * WR[c * np + i];
+        for (int q = r0; q < r1; ++q) {
+            const int jn = __ldg(&tp.ring_idx[q]);
+            const T ct = __ldg(&tp.ring_ct[q]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gb[c] += ct * WR[c * np + jn];
+        }
         T g2 = T(0), ei = T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T du = U[c * np + i] - UY[c * np + i];
-            const T gv = Gout[c * np + i] + volc * GC[c * np + i] + m * ms * du;
+            const T gv = Gout[c * np + i] + gb[c] + volc * GC[c * np + i] + m * ms * du;
             Gout[c * np + i] = gv;
             ei += T(0.5) * m * ms * du * du;
             g2 += gv * gv;
         }
-        acc2[0].add(ei);
-        acc2[1].add(hm * hm * g2);
+        ci[0].add(ei);
+        pr[0] += hm * hm * g2;
     }
-    const double inv_n = 1.0 / (double)n, inv_lbar = (double)tp.inv_lbar, uT = Unit<T>::u;
-    block_reduce<T, 2>(acc2, smem, [=](CellShared* s) {
+    const T inv_n = T(1) / T(n), inv_lbar = tp.inv_lbar;
+    const double uT = Unit<T>::u;
+    block_reduce_cp<T, 1, 1>(ci, pr, smem, [=](CellShared* s) {
         s->Ein = s->out[0];
         s->E = s->Ein + s->Earea + s->Esk + s->Ebend + s->Evol;
-        s->res = sqrt(s->out[1] * inv_n) * inv_lbar;
+        s->res = (double)(sqrt((T)s->out[1] * inv_n) * inv_lbar);
         s->noise = 4.0 * uT * (s->noise + 2.0 * s->Ein);
     });
 }
 
-// R = A^-1 Q for the three coordinate rows (A symmetric: column access is
-// coalesced across the lanes of a warp, Q is broadcast from shared memory).
+// R = A^-1 Q for the three coordinate rows.
+// FP32: a warp owns a tile of 128 rows (4 consecutive rows per lane, float4 loads of
+// the symmetric A^-1 by columns, coalesced) and a share of the j range; Q is
+// broadcast from shared memory.  The warps' partial sums go to `scratch` (the
+// triangle buffer, idle outside the objective evaluation) and are added in a fixed
+// order, so the result is deterministic.
 template <typename T>
-__device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R)
+__device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch)
 {
     const int n = tp.n, np = tp.n_pad, N3 = 3 * np;
-    for (int e = threadIdx.x; e < N3; e += blockDim.x) R[e] = T(0);
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int ntile = (n + 31) >> 5;
-    int nsplit = 8;
-    for (int s = 1; s <= 8; ++s) {
-        const int items = ntile * s, rounds = (items + nw - 1) / nw;
-        if (items * 10 >= rounds * nw * 9) {
-            nsplit = s;
-            break;
-        }
-    }
-    const int chunk = (((n + nsplit - 1) / nsplit) + 3) & ~3;  // multiple of 4: aligned vector loads of Q
     const T* __restrict__ A = tp.ainv;
-    for (int item = warp; item < ntile * nsplit; item += nw) {
-        const int rt = item / nsplit, js = item - rt * nsplit;
-        const int row = rt * 32 + lane;
-        const int j0 = js * chunk, j1 = min(n, j0 + chunk);
-        T a0 = T(0), a1 = T(0), a2 = T(0);
-        if (row < n && j0 < j1) {
-            int j = j0;
-            for (; j + 4 <= j1; j += 4) {
-                T av[4], q0[4], q1[4], q2[4];
+    if constexpr (sizeof(T) == 4) {
+        const int ntile = (n + 127) >> 7;
+        // ntile <= nw: warp w takes tile w % ntile and a share of the j range;
+        // ntile > nw: warps loop over whole tiles.  Partials go to scratch[item][c][128].
+        const bool split = ntile <= nw;
+        for (int item = warp; item < (split ? nw : ntile); item += nw) {
+            const int tile = split ? item % ntile : item;
+            const int part = split ? item / ntile : 0;
+            const int nparts = split ? (nw - 1 - tile) / ntile + 1 : 1;
+            const int chunk = (((n + nparts - 1) / nparts) + 3) & ~3;
+            const int j0 = part * chunk, j1 = min(n, j0 + chunk);
+            const int row0 = tile * 128 + 4 * lane;
+            float acc[3][4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) av[u] = __ldg(&A[(size_t)(j + u) * np + row]);
-                if constexpr (sizeof(T) == 4) {
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[c][r] = 0.f;
+            if (row0 < n) {
+                int j = j0;
+                for (; j + 4 <= j1; j += 4) {
+                    float4 av[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        av[u] = __ldg(reinterpret_cast<const float4*>(A + (size_t)(j + u) * np + row0));
                     const float4 x0 = *reinterpret_cast<const float4*>(Q + j);
                     const float4 x1 = *reinterpret_cast<const float4*>(Q + np + j);
                     const float4 x2 = *reinterpret_cast<const float4*>(Q + 2 * np + j);
-                    q0[0] = x0.x; q0[1] = x0.y; q0[2] = x0.z; q0[3] = x0.w;
-                    q1[0] = x1.x; q1[1] = x1.y; q1[2] = x1.z; q1[3] = x1.w;
-                    q2[0] = x2.x; q2[1] = x2.y; q2[2] = x2.z; q2[3] = x2.w;
-                } else {
+                    const float q0[4] = {x0.x, x0.y, x0.z, x0.w}, q1[4] = {x1.x, x1.y, x1.z, x1.w},
+                                q2[4] = {x2.x, x2.y, x2.z, x2.w};
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        q0[u] = Q[j + u];
-                        q1[u] = Q[np + j + u];
-                        q2[u] = Q[2 * np + j + u];
+                        const float a4[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            acc[0][r] += a4[r] * q0[u];
+                            acc[1][r] += a4[r] * q1[u];
+                            acc[2][r] += a4[r] * q2[u];
+                        }
                     }
                 }
+                for (; j < j1; ++j) {
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(A + (size_t)j * np + row0));
+                    const float a4[4] = {a.x, a.y, a.z, a.w};
+                    const float qq[3] = {Q[j], Q[np + j], Q[2 * np + j]};
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    a0 += av[u] * q0[u];
-                    a1 += av[u] * q1[u];
-                    a2 += av[u] * q2[u];
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) acc[c][r] += a4[r] * qq[c];
                 }
             }
-            for (; j < j1; ++j) {
-                const T av = __ldg(&A[(size_t)j * np + row]);
-                a0 += av * Q[j];
-                a1 += av * Q[np + j];
-                a2 += av * Q[2 * np + j];
-            }
-            atomicAdd(&R[row], a0);
-            atomicAdd(&R[np + row], a1);
-            atomicAdd(&R[2 * np + row], a2);
+            float* P = reinterpret_cast<float*>(scratch) + item * 384;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                *reinterpret_cast<float4*>(P + c * 128 + 4 * lane) =
+                    make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
         }
+        __syncthreads();
+        const float* S = reinterpret_cast<const float*>(scratch);
+        for (int e = threadIdx.x; e < N3; e += blockDim.x) {
+            const int c = e / np, row = e - c * np;
+            float s = 0.f;
+            if (row < n) {
+                const int tl = row >> 7, rr = row & 127;
+                if (split) {
+                    for (int w = tl; w < nw; w += ntile) s += S[w * 384 + c * 128 + rr];
+                } else {
+                    s = S[tl * 384 + c * 128 + rr];
+                }
+            }
+            R[e] = s;
+        }
+        __syncthreads();
+    } else {
+        for (int e = threadIdx.x; e < N3; e += blockDim.x) R[e] = T(0);
+        __syncthreads();
+        const int ntile = (n + 31) >> 5;
+        for (int item = warp; item < ntile; item += nw) {
+            const int row = item * 32 + lane;
+            if (row < n) {
+                T a0 = T(0), a1 = T(0), a2 = T(0);
+                for (int j = 0; j < n; ++j) {
+                    const T av = __ldg(&A[(size_t)j * np + row]);
+                    a0 += av * Q[j];
+                    a1 += av * Q[np + j];
+                    a2 += av * Q[2 * np + j];
+                }
+                R[row] = a0;
+                R[np + row] = a1;
+                R[2 * np + row] = a2;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 template <typename T>
@@ -494,6 +670,8 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
     T* GCv = vec_ptr(gd, smem, slot, V_GC);
     T* UYv = vec_ptr(gd, smem, slot, V_UY);
     T* Dv = vec_ptr(gd, smem, slot, V_D);
+    T* TRIv = vec_ptr(gd, smem, slot, V_TRI);
+    T* WRv = vec_ptr(gd, smem, slot, V_WR);
     const int M = a.p.lbfgs_m;
 
     const long long so = gd.state_off + cell * 3LL * n;
@@ -527,7 +705,7 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
     volume_at_xn(tp, XN, smem);
     const double Vn = sh->V;
 
-    evaluate(tp, XN, u, UYv, g, GCv, Vn, smem);
+    evaluate(tp, XN, u, UYv, g, GCv, TRIv, WRv, Vn, smem);
     int evals = 1, iters = 0, status = NPFEM_CELL_OK;
 
     if (eval_mode) {
@@ -562,55 +740,47 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
             const int i = (head - 1 - q + M) % M;
             const T* S = vec_ptr(gd, smem, slot, V_SBASE + i);
             const T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + i);
-            Acc<T> acc[1];
-            T s = T(0);
-            for (int e = tid; e < N3; e += NT) s += S[e] * Dv[e];
-            acc[0].add(s);
-            block_reduce<T, 1>(acc, smem, [=](CellShared* c) { c->alpha[i] = c->rho[i] * c->out[0]; });
+            T s[1] = {T(0)};
+            for (int e = tid; e < N3; e += NT) s[0] += S[e] * Dv[e];
+            block_sum<T, 1>(s, smem, [=](CellShared* c) { c->alpha[i] = c->rho[i] * c->out[0]; });
             const T al = (T)sh->alpha[i];
             for (int e = tid; e < N3; e += NT) Dv[e] -= al * Y[e];
         }
         // r = H0 q through the dense inverse (contract_simt syncs before reading q)
-        contract_simt(tp, Dv, GCv);
+        contract_simt(tp, Dv, GCv, TRIv);
         // second loop: beta = rho_i y_i^T r; r += s_i (alpha_i - beta) (oldest first)
         for (int q = count - 1; q >= 0; --q) {
             const int i = (head - 1 - q + M) % M;
             const T* S = vec_ptr(gd, smem, slot, V_SBASE + i);
             const T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + i);
-            Acc<T> acc[1];
-            T s = T(0);
-            for (int e = tid; e < N3; e += NT) s += Y[e] * GCv[e];
-            acc[0].add(s);
-            block_reduce<T, 1>(acc, smem, [=](CellShared* c) { c->out[1] = c->alpha[i] - c->rho[i] * c->out[0]; });
+            T s[1] = {T(0)};
+            for (int e = tid; e < N3; e += NT) s[0] += Y[e] * GCv[e];
+            block_sum<T, 1>(s, smem, [=](CellShared* c) { c->out[1] = c->alpha[i] - c->rho[i] * c->out[0]; });
             const T coef = (T)sh->out[1];
             for (int e = tid; e < N3; e += NT) GCv[e] += S[e] * coef;
         }
         double gdv;
         {
-            Acc<T> acc[1];
-            T s = T(0);
+            T s[1] = {T(0)};
             for (int e = tid; e < N3; e += NT) {
                 const T dv = -GCv[e];
                 Dv[e] = dv;
-                s += g[e] * dv;
+                s[0] += g[e] * dv;
             }
-            acc[0].add(s);
-            block_reduce<T, 1>(acc, smem);
+            block_sum<T, 1>(s, smem);
             gdv = sh->out[0];
         }
         if (!(gdv < 0.0)) {
             // not a descent direction: drop the history, d = -H~^-1 g
             count = 0;
-            contract_simt(tp, g, GCv);
-            Acc<T> acc[1];
-            T s = T(0);
+            contract_simt(tp, g, GCv, TRIv);
+            T s[1] = {T(0)};
             for (int e = tid; e < N3; e += NT) {
                 const T dv = -GCv[e];
                 Dv[e] = dv;
-                s += g[e] * dv;
+                s[0] += g[e] * dv;
             }
-            acc[0].add(s);
-            block_reduce<T, 1>(acc, smem);
+            block_sum<T, 1>(s, smem);
             gdv = sh->out[0];
         }
 
@@ -622,7 +792,7 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
             const T al = (T)alpha;
             for (int e = tid; e < N3; e += NT) ut[e] = u[e] + al * Dv[e];
             __syncthreads();
-            evaluate(tp, XN, ut, UYv, gt, GCv, Vn, smem);
+            evaluate(tp, XN, ut, UYv, gt, GCv, TRIv, WRv, Vn, smem);
             ++evals;
             if (tid == 0) {
                 const bool ok = !sh->bad && sh->E <= E + c1 * alpha * gdv + anoise * (sh->noise + noiseE);
@@ -642,21 +812,16 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
         // history pair (s, y) = (x_{k+1} - x_k, grad_{k+1} - grad_k), kept when the
         // curvature condition holds and s^T y > 0
         if (M > 0) {
-            Acc<T> acc[4];
-            T sy = T(0), ss = T(0), yy = T(0), gtd = T(0);
+            T acc[4] = {T(0), T(0), T(0), T(0)};  // s^T y, s^T s, y^T y, grad_new^T d
             for (int e = tid; e < N3; e += NT) {
                 const T se = ut[e] - u[e], ye = gt[e] - g[e];
-                sy += se * ye;
-                ss += se * se;
-                yy += ye * ye;
-                gtd += gt[e] * Dv[e];
+                acc[0] += se * ye;
+                acc[1] += se * se;
+                acc[2] += ye * ye;
+                acc[3] += gt[e] * Dv[e];
             }
-            acc[0].add(sy);
-            acc[1].add(ss);
-            acc[2].add(yy);
-            acc[3].add(gtd);
             const int hd = head;
-            block_reduce<T, 4>(acc, smem, [=](CellShared* c) {
+            block_sum<T, 4>(acc, smem, [=](CellShared* c) {
                 c->push = c->out[3] >= c2 * gdv && c->out[0] > 1e-12 * sqrt(c->out[1] * c->out[2]);
                 if (c->push) c->rho[hd] = 1.0 / c->out[0];
             });

@@ -86,7 +86,7 @@ int run_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells, 
         g.state_off = state;
         g.cells = cells[gi];
         long long sb = 0;
-        place_vectors(&g, h->n_pad, h0->opts.lbfgs_m, budget, &sb);
+        place_vectors(&g, h->n_pad, h->nt, h0->opts.lbfgs_m, budget, &sb);
         slot = std::max(slot, sb);
         smem_max = std::max(smem_max, g.smem_bytes);
         total += cells[gi];
