@@ -287,9 +287,12 @@ def main():
     plain = None
     if not args.no_plain and args.precision != "fp32":
         hp = N.Handle(pop["rest"], pop["tris"], N.material(), N.default_opts(precision="fp32"), dt=DT, device=local)
-        tp, _, _, _, _ = device_leg(N, W, hp, pop, cells, max(10, args.steps // 4), 2, torch, flush)
-        plain = {"value": max_over_ranks(pg, 0) or total_cells * len(tp) / (sum(tp) / 1e3), "unit": "RBC-steps/s",
-                 "precision": "fp32"}
+        ksteps = max(10, args.steps // 4)
+        tp, pit, pev, pst, pres = device_leg(N, W, hp, pop, cells, ksteps, 2, torch, flush)
+        plain = {"value": total_cells * ksteps / max_over_ranks(pg, sum(tp) / 1e3), "unit": "RBC-steps/s",
+                 "precision": "fp32", "steps": ksteps, "iterations_per_cell": pit / cells,
+                 "residual_max": pres, "status_counts": pst.tolist()}
+        del hp
 
     e2e = None
     if not args.no_e2e:

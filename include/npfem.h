@@ -54,9 +54,13 @@ extern "C" {
 #define NPFEM_PREC_FP64 0 /* state, energies and the A^-1 contraction in FP64            */
 #define NPFEM_PREC_FP32 1 /* state and energies FP32 (sums FP64), A^-1 FP32 on the SIMT  */
                           /* pipes: the plain GPU path                                  */
-#define NPFEM_PREC_TF32 2 /* as FP32, A^-1 contraction on tcgen05 tensor cores in TF32    */
-                          /* with FP32 accumulation plus one refinement sweep           */
-#define NPFEM_PREC_BF16 3 /* as TF32 but BF16 operands                                   */
+#define NPFEM_PREC_TF32 2 /* reserved: a TF32 row block of A^-1 does not fit in tensor    */
+                          /* memory; npfem_create rejects it                             */
+#define NPFEM_PREC_BF16 3 /* as FP32, but the A^-1 contraction runs on tcgen05 tensor    */
+                          /* cores: BF16 A^-1 resident in tensor memory across a cluster */
+                          /* of ceil(n/128) SMs, BF16 q, FP32 accumulation, `refine`     */
+                          /* refinement sweeps; meshes above 960 vertices fall back to    */
+                          /* the FP32 SIMT contraction                                    */
 
 typedef struct npfem_handle npfem_handle;
 
@@ -93,7 +97,9 @@ typedef struct {
    fixed_alpha: 1 = always take alpha = 1 (the local/global solver of Appendix A).
    equal_mass: 1 = lump the mass equally, 0 = by barycentric rest area.
    armijo_noise: multiple of the estimated rounding error of g added to the
-                 Armijo bound (FP32 energies); 0 = exact test. */
+                 Armijo bound (FP32 energies); 0 = exact test.
+   refine: NPFEM_PREC_BF16 only: refinement sweeps of the tensor-core A^-1
+           contraction (0 or 1): r = A^-1 q, then r += A^-1 (q - H~ r). */
 typedef struct {
     int32_t precision;
     int32_t lbfgs_m;
@@ -104,6 +110,7 @@ typedef struct {
     int32_t fixed_alpha;
     int32_t equal_mass;
     double armijo_noise;
+    int32_t refine;
 } npfem_opts;
 
 /* Per-cell result of one npfem_step call (device memory, 32 bytes). */
@@ -118,7 +125,7 @@ typedef struct {
 
 /* Fills *o with the defaults used throughout the library: FP32, m = 5,
    max_iter = 50, tol = 1e-6, c1 = 1e-4, c2 = 0.9, 30 halvings, area-lumped mass,
-   armijo_noise = 4. */
+   armijo_noise = 4, refine = 1. */
 void npfem_default_opts(npfem_opts* o);
 
 /* Creates a handle for one mesh topology on CUDA device `device` and time step dt
@@ -191,6 +198,12 @@ int npfem_get_inverse(npfem_handle* h, double* out_host);
 /* Copies per-vertex lumped masses (n_verts doubles) and the scalars
    {V0, A0, mean rest edge length, total mass} (4 doubles) to host memory. */
 int npfem_get_rest_info(npfem_handle* h, double* masses_host, double* scalars_host);
+
+/* Synchronises the handle's device and reports whether a bounded device-side wait
+   of a previous step gave up (the tensor-core path waits for its MMAs with an
+   iteration limit): returns NPFEM_ERR_TIMEOUT and clears the flag if so, else 0.
+   Errors: INVALID_ARG, CUDA. */
+int npfem_check_device(npfem_handle* h);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* npfem_last_error(void);

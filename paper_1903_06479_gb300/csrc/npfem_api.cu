@@ -135,6 +135,11 @@ int check_opts(const npfem_opts* o)
     if (!(o->tol >= 0.0) || !(o->c1 > 0.0 && o->c1 < 1.0) || !(o->c2 > o->c1 && o->c2 < 1.0) ||
         !(o->armijo_noise >= 0.0))
         return fail(NPFEM_ERR_INVALID_ARG, "opts: need tol >= 0, 0 < c1 < c2 < 1, armijo_noise >= 0");
+    if (o->refine < 0 || o->refine > 1) return fail(NPFEM_ERR_INVALID_ARG, "opts.refine must be 0 or 1");
+    if (o->precision == NPFEM_PREC_TF32)
+        return fail(NPFEM_ERR_INVALID_ARG,
+                    "NPFEM_PREC_TF32 is not available: a TF32 row block of A^-1 does not fit in tensor memory; "
+                    "use NPFEM_PREC_BF16");
     return 0;
 }
 
@@ -208,6 +213,68 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     return 0;
 }
 
+// One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
+int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
+                 cudaStream_t stream)
+{
+    if (cells == 0) return 0;
+    LaunchArgs<float> a;
+    memset(&a, 0, sizeof(a));
+    GroupDesc<float>& g = a.g[0];
+    g.topo = h->tf;
+    g.cell_begin = 0;
+    g.state_off = 0;
+    g.cells = cells;
+    const int cluster = h->tf.rb;
+    const int ncol = cluster * 3 > 16 ? 32 : 16;
+    const int bbytes = (ncol * h->tf.kpad * 2 + 127) & ~127;
+    const int budget = h->smem_optin - kFixedSmem - 1024 - bbytes;
+    long long slot = 0;
+    place_vectors(&g, h->n_pad, h->nt, h->opts.lbfgs_m, budget, &slot, bbytes);
+    a.n_groups = 1;
+    a.total_cells = cells;
+    a.x = x;
+    a.v = v;
+    a.f = f;
+    a.stats = stats;
+    a.work = h->work;
+    a.p.lbfgs_m = h->opts.lbfgs_m;
+    a.p.max_iter = h->opts.max_iter;
+    a.p.max_halvings = h->opts.max_halvings;
+    a.p.fixed_alpha = h->opts.fixed_alpha;
+    a.p.tol = h->opts.tol;
+    a.p.c1 = h->opts.c1;
+    a.p.c2 = h->opts.c2;
+    a.p.armijo_noise = h->opts.armijo_noise;
+    a.p.mode = 0;
+    a.p.contraction = CONTRACT_TC_BF16;
+    a.p.cluster = cluster;
+    a.p.refine = h->opts.refine;
+    // one block per SM: a second block on the SM would wait in the tensor-memory
+    // allocation while its cluster waits for it
+    int smem = kFixedSmem + g.smem_bytes;
+    smem = std::max(smem, h->smem_optin / 2 + 4096);
+    a.slot_bytes = slot;
+    const long long max_grid = (long long)h->sm_count;
+    if (slot > 0) {
+        size_t need = (size_t)slot * (size_t)max_grid;
+        if (need > h->scratch_bytes) {
+            if (h->scratch) {
+                NPFEM_CUDA(cudaStreamSynchronize(stream));
+                cudaFree(h->scratch);
+                h->scratch = nullptr;
+                h->scratch_bytes = 0;
+            }
+            NPFEM_CUDA(cudaMalloc(&h->scratch, need));
+            h->scratch_bytes = need;
+        }
+        a.scratch = h->scratch;
+    }
+    int grid = 0;
+    NPFEM_CUDA(launch_cells_tc(a, cluster, h->threads, smem, stream, &grid));
+    return 0;
+}
+
 int validate_group(npfem_handle* const* meshes, int n_groups, const int32_t* cells)
 {
     if (!meshes || n_groups < 1 || n_groups > kMaxGroups || !cells)
@@ -239,6 +306,7 @@ void npfem_default_opts(npfem_opts* o)
     o->fixed_alpha = 0;
     o->equal_mass = 0;
     o->armijo_noise = 4.0;
+    o->refine = 1;
 }
 
 const char* npfem_last_error(void) { return g_last_error.c_str(); }
@@ -325,6 +393,24 @@ int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_
         return bail(fail(NPFEM_ERR_CUDA, "publishing A^-1 failed"));
     rc = h->precision == NPFEM_PREC_FP64 ? fill_topo<double>(h, &h->td, ainv_t) : fill_topo<float>(h, &h->tf, ainv_t);
     if (rc) return bail(rc);
+    if (h->precision == NPFEM_PREC_BF16) {
+        // tensor-core path: BF16 A^-1 in 128-row blocks with K padded to 16, and L for
+        // the refinement residual
+        const int kpad = (n + 15) & ~15, rb = (n + 127) / 128;
+        void* abf = h->alloc<unsigned short>((size_t)rb * 128 * kpad, &e);
+        if (e) return bail(e);
+        if (publish_inverse_bf16_blocked(h->ainv64, n, rb * 128, kpad, abf, 0) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            return bail(fail(NPFEM_ERR_CUDA, "publishing the BF16 A^-1 failed"));
+        h->tf.ainv_lp = abf;
+        h->tf.kpad = kpad;
+        h->tf.rb = rb;
+        std::vector<float> lval(h->host.L_val.begin(), h->host.L_val.end());
+        std::vector<unsigned short> lidx(h->host.L_idx.begin(), h->host.L_idx.end());
+        if ((rc = upload(h, h->host.L_ptr, &h->tf.h_ptr))) return bail(rc);
+        if ((rc = upload(h, lidx, &h->tf.h_idx))) return bail(rc);
+        if ((rc = upload(h, lval, &h->tf.h_val))) return bail(rc);
+    }
     *out = h;
     return 0;
 }
@@ -350,6 +436,21 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
     DeviceGuard guard(meshes[0]->device);
     std::lock_guard<std::mutex> lk(meshes[0]->mu);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (meshes[0]->precision == NPFEM_PREC_BF16) {
+        bool all_tc = true;
+        for (int g = 0; g < n_groups; ++g) all_tc = all_tc && meshes[g]->n <= kTcMaxVerts;
+        if (all_tc) {
+            long long cell0 = 0, state0 = 0;
+            for (int g = 0; g < n_groups; ++g) {
+                int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + state0, (float*)v + state0,
+                                      (const float*)f_ext + state0, stats ? stats + cell0 : nullptr, s);
+                if (rc) return rc;
+                cell0 += cells_per_group[g];
+                state0 += 3LL * meshes[g]->n * cells_per_group[g];
+            }
+            return 0;
+        }
+    }
     if (meshes[0]->precision == NPFEM_PREC_FP64)
         return run_cells<double>(meshes, n_groups, cells_per_group, (double*)x, (double*)v, (const double*)f_ext,
                                  nullptr, nullptr, nullptr, stats, 0, s);
@@ -413,6 +514,20 @@ int npfem_eval(npfem_handle* h, int n_cells, const void* x, const void* y, void*
                                  nullptr, 1, s);
     return run_cells<float>(hs, 1, &cells, (float*)x, nullptr, nullptr, (const float*)y, (float*)grad, parts, nullptr,
                             1, s);
+}
+
+int npfem_check_device(npfem_handle* h)
+{
+    if (!h) return fail(NPFEM_ERR_INVALID_ARG, "null handle");
+    DeviceGuard guard(h->device);
+    NPFEM_CUDA(cudaDeviceSynchronize());
+    unsigned flag = 0;
+    NPFEM_CUDA(cudaMemcpy(&flag, h->work + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (flag) {
+        NPFEM_CUDA(cudaMemset(h->work + 2, 0, sizeof(unsigned)));
+        return fail(NPFEM_ERR_TIMEOUT, "a bounded device wait gave up in a previous step (tensor-core MMA completion)");
+    }
+    return 0;
 }
 
 int npfem_get_inverse(npfem_handle* h, double* out_host)

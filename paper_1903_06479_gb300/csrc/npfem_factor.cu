@@ -76,7 +76,23 @@ __global__ void symmetrise_publish(const double* A, int n, int n_pad, float* o32
     }
 }
 
+__global__ void publish_bf16_blocked(const double* A, int n, int rows_pad, int kpad, __nv_bfloat16* out)
+{
+    size_t total = (size_t)rows_pad * kpad;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(q / kpad), j = (int)(q % kpad);
+        double v = (i < n && j < n) ? A[(size_t)i * n + j] : 0.0;
+        out[q] = __double2bfloat16(v);
+    }
+}
+
 }  // namespace
+
+cudaError_t publish_inverse_bf16_blocked(const double* A, int n, int rows_pad, int kpad, void* out, cudaStream_t s)
+{
+    publish_bf16_blocked<<<1024, 256, 0, s>>>(A, n, rows_pad, kpad, (__nv_bfloat16*)out);
+    return cudaGetLastError();
+}
 
 cudaError_t invert_spd_fp64(double* A, int n, double* col, int* d_flag, cudaStream_t s)
 {

@@ -47,9 +47,10 @@ struct TopoDev {
     const unsigned* inc_idx;     // [3 nt] (triangle << 2) | corner
     const T* ainv;               // [n_pad][n_pad] A^-1 in T (zero padding)
     const void* ainv_lp;         // A^-1 for the tensor-core contraction (bf16 or tf32-rounded fp32)
-    const int* h_ptr;            // sparse H~ (CSR, fp32) for the refinement sweep
+    const int* h_ptr;            // L (CSR, fp32) for the refinement residual q - H~ r
     const unsigned short* h_idx;
     const float* h_val;
+    int kpad, rb;                // tensor-core path: K padded to 16, row blocks of 128
     T C, B, Dsk, kvol;           // material
     T h, inv_h2, inertia_scale;  // time step; inertia_scale = 1 + h alpha_D
     T kappa, lbar, inv_lbar;
@@ -72,6 +73,8 @@ struct SolverParams {
     double tol, c1, c2, armijo_noise;
     int mode;         // 0 = time step, 1 = objective/gradient evaluation only
     int contraction;  // Contraction
+    int cluster;      // tensor-core path: blocks per cluster (= row blocks of A^-1)
+    int refine;       // tensor-core path: refinement sweeps (0 or 1)
 };
 
 template <typename T>
@@ -88,7 +91,7 @@ struct LaunchArgs {
     npfem_cell_stats* stats;
     char* scratch;     // per-CTA global slots for vectors that do not fit in smem
     long long slot_bytes;
-    unsigned int* work;  // [0] next work item, [1] finished CTAs (reset by the last CTA)
+    unsigned int* work;  // [0] next work item, [1] finished blocks (reset by the last block), [2] error flag
     SolverParams p;
 };
 
@@ -118,11 +121,21 @@ cudaError_t invert_spd_fp64(double* A, int n, double* col_scratch, int* d_flag, 
 // Symmetrise A^-1 (FP64, n x n) and write padded copies in fp32 / fp64 / bf16.
 cudaError_t publish_inverse(const double* A, int n, int n_pad, float* out32, double* out64, void* out_bf16,
                             float* out_tf32, cudaStream_t s);
+// A^-1 in BF16 as [rows_pad][kpad] (zero padding), the layout the tensor-core path
+// loads into tensor memory.
+cudaError_t publish_inverse_bf16_blocked(const double* A, int n, int rows_pad, int kpad, void* out, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s);
 template <typename T>
 cudaError_t set_cell_kernel_smem(int bytes);
+// Tensor-core (BF16, A^-1 row blocks resident in TMEM across a cluster) launch of one
+// mesh group; sets *grid_out.
+cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, int smem, cudaStream_t s,
+                            int* grid_out);
+// Largest mesh the tensor-core path takes: A block (kpad / 2 columns) plus a
+// 32-column accumulator within 512 TMEM columns, and at most 8 blocks per cluster.
+constexpr int kTcMaxVerts = 960;
 
 // Records msg as the calling thread's last error and returns code (npfem_api.cu).
 int set_error(int code, const std::string& msg);

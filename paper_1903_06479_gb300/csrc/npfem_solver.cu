@@ -16,8 +16,10 @@
 // no per-thread FP64 arithmetic: block sums are compensated FP32 pairs (error-free
 // two-sum), and the few scalar FP64 operations per reduction run on one thread
 // and are broadcast through shared memory.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "npfem_internal.h"
 
@@ -68,6 +70,10 @@ struct CellShared {
     double alpha[kMaxHistory];
     double post[12];         // centre of mass, its velocity, angular velocity
     double volc;
+    long long item;          // work item handed to the block
+    unsigned long long mbar; // tensor-core path: MMA completion barrier
+    unsigned need[16];       // tensor-core path: request flags of the cluster's blocks
+    unsigned taddr;          // tensor-core path: tensor-memory base address
     int bad;
     int accept;
     int push;
@@ -653,35 +659,58 @@ __device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch
     }
 }
 
+// ---------------------------------------------------------------------------------
+// One cell's quasi-Newton solve, split into the phases that both kernels drive.
+// All threads of the block call every method (control flow is block-uniform).
+// ---------------------------------------------------------------------------------
 template <typename T>
-__device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long long cell, long long item,
-                           unsigned char* smem)
-{
-    const TopoDev<T>& tp = gd.topo;
-    const int n = tp.n, np = tp.n_pad, N3 = 3 * np, tid = threadIdx.x, NT = blockDim.x;
-    CellShared* sh = cell_shared(smem);
-    char* slot = a.scratch ? a.scratch + (long long)blockIdx.x * a.slot_bytes : nullptr;
+struct CellSolver {
+    const LaunchArgs<T>* a;
+    const GroupDesc<T>* gd;
+    unsigned char* smem;
+    char* slot;
+    CellShared* sh;
+    T *XN, *u, *ut, *g, *gt, *GCv, *UYv, *Dv, *TRIv, *WRv;
+    long long so, item;
+    int M, head, count, iters, evals, status;
+    double E, noiseE, res, Vlast, Vn, gdv;
+    bool nonfinite;
 
-    T* XN = vec_ptr(gd, smem, slot, V_XN);
-    T* u = vec_ptr(gd, smem, slot, V_U);
-    T* ut = vec_ptr(gd, smem, slot, V_UT);
-    T* g = vec_ptr(gd, smem, slot, V_G);
-    T* gt = vec_ptr(gd, smem, slot, V_GT);
-    T* GCv = vec_ptr(gd, smem, slot, V_GC);
-    T* UYv = vec_ptr(gd, smem, slot, V_UY);
-    T* Dv = vec_ptr(gd, smem, slot, V_D);
-    T* TRIv = vec_ptr(gd, smem, slot, V_TRI);
-    T* WRv = vec_ptr(gd, smem, slot, V_WR);
-    const int M = a.p.lbfgs_m;
+    __device__ const TopoDev<T>& tp() const { return gd->topo; }
+    __device__ T* hist(int v) const { return vec_ptr(*gd, smem, slot, v); }
 
-    const long long so = gd.state_off + cell * 3LL * n;
-    const T h = tp.h;
-    const T inv_ms = T(1) / tp.inertia_scale;
-    const bool eval_mode = a.p.mode == 1;
-
-    // ---- load the cell: local coordinates around vertex 0, first guess
+    __device__ void bind(const LaunchArgs<T>& la, const GroupDesc<T>& g_, unsigned char* sm)
     {
-        const T* x = a.x + so;
+        a = &la;
+        gd = &g_;
+        smem = sm;
+        sh = cell_shared(sm);
+        slot = la.scratch ? la.scratch + (long long)blockIdx.x * la.slot_bytes : nullptr;
+        XN = vec_ptr(g_, sm, slot, V_XN);
+        u = vec_ptr(g_, sm, slot, V_U);
+        ut = vec_ptr(g_, sm, slot, V_UT);
+        g = vec_ptr(g_, sm, slot, V_G);
+        gt = vec_ptr(g_, sm, slot, V_GT);
+        GCv = vec_ptr(g_, sm, slot, V_GC);
+        UYv = vec_ptr(g_, sm, slot, V_UY);
+        Dv = vec_ptr(g_, sm, slot, V_D);
+        TRIv = vec_ptr(g_, sm, slot, V_TRI);
+        WRv = vec_ptr(g_, sm, slot, V_WR);
+        M = la.p.lbfgs_m;
+    }
+
+    // Load the cell (local coordinates around vertex 0), first guess, V(x_n), g and
+    // grad g at x^(1).  In evaluation mode writes the gradient and parts and returns
+    // false.
+    __device__ bool begin(long long cell, long long it)
+    {
+        const TopoDev<T>& T_ = tp();
+        const int n = T_.n, np = T_.n_pad, N3 = 3 * np, tid = threadIdx.x, NT = blockDim.x;
+        item = it;
+        so = gd->state_off + cell * 3LL * n;
+        const T h = T_.h, inv_ms = T(1) / T_.inertia_scale;
+        const bool eval_mode = a->p.mode == 1;
+        const T* x = a->x + so;
         const T o0 = x[0], o1 = x[n], o2 = x[2 * n];
         for (int e = tid; e < N3; e += NT) {
             const int c = e / np, i = e - c * np;
@@ -690,113 +719,130 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
                 const T xv = x[c * n + i];
                 xn = xv - (c == 0 ? o0 : (c == 1 ? o1 : o2));
                 if (eval_mode) {
-                    uy = a.y[so + c * n + i] - xv;
+                    uy = a->y[so + c * n + i] - xv;
                 } else {
-                    const T vv = a.v[so + c * n + i], fv = a.f[so + c * n + i];
-                    uy = (h * vv + h * h * fv * __ldg(&tp.inv_mass[i])) * inv_ms;
+                    const T vv = a->v[so + c * n + i], fv = a->f[so + c * n + i];
+                    uy = (h * vv + h * h * fv * __ldg(&T_.inv_mass[i])) * inv_ms;
                 }
             }
             XN[e] = xn;
             UYv[e] = uy;
             u[e] = eval_mode ? T(0) : uy;
         }
-    }
-    __syncthreads();
-    volume_at_xn(tp, XN, smem);
-    const double Vn = sh->V;
-
-    evaluate(tp, XN, u, UYv, g, GCv, TRIv, WRv, Vn, smem);
-    int evals = 1, iters = 0, status = NPFEM_CELL_OK;
-
-    if (eval_mode) {
-        for (int e = tid; e < 3 * n; e += NT) {
-            const int c = e / n, i = e - c * n;
-            a.grad_out[so + e] = g[c * np + i];
-        }
-        if (tid == 0) {
-            double* P = a.parts + 8 * item;
-            P[0] = sh->Ein; P[1] = sh->Earea; P[2] = sh->Esk; P[3] = sh->Ebend; P[4] = sh->Evol;
-            P[5] = sh->V; P[6] = sh->E; P[7] = sh->res;
-        }
         __syncthreads();
-        return;
+        volume_at_xn(T_, XN, smem);
+        Vn = sh->V;
+        evaluate(T_, XN, u, UYv, g, GCv, TRIv, WRv, Vn, smem);
+        evals = 1;
+        iters = 0;
+        status = NPFEM_CELL_OK;
+        head = 0;
+        count = 0;
+        if (eval_mode) {
+            for (int e = tid; e < 3 * n; e += NT) {
+                const int c = e / n, i = e - c * n;
+                a->grad_out[so + e] = g[c * np + i];
+            }
+            if (tid == 0) {
+                double* P = a->parts + 8 * item;
+                P[0] = sh->Ein; P[1] = sh->Earea; P[2] = sh->Esk; P[3] = sh->Ebend; P[4] = sh->Evol;
+                P[5] = sh->V; P[6] = sh->E; P[7] = sh->res;
+            }
+            __syncthreads();
+            return false;
+        }
+        E = sh->E;
+        noiseE = sh->noise;
+        res = sh->res;
+        Vlast = sh->V;
+        nonfinite = sh->bad || !isfinite(sh->E) || !isfinite(sh->res);
+        return true;
     }
 
-    // ---- quasi-Newton iterations (L-BFGS, Nocedal & Wright Algorithm 7.4, H0 = H~^-1)
-    int head = 0, count = 0;
-    double E = sh->E, noiseE = sh->noise, res = sh->res, Vlast = sh->V;
-    bool nonfinite = sh->bad || !isfinite(sh->E) || !isfinite(sh->res);
-    const double c1 = a.p.c1, c2 = a.p.c2, anoise = a.p.armijo_noise;
-    while (!nonfinite) {
-        if (res <= a.p.tol) break;
-        if (iters >= a.p.max_iter) {
+    // Residual test and iteration cap; false when the cell is finished.
+    __device__ bool wants_direction()
+    {
+        if (nonfinite) return false;
+        if (res <= a->p.tol) return false;
+        if (iters >= a->p.max_iter) {
             status = NPFEM_CELL_MAXITER;
-            break;
+            return false;
         }
+        return true;
+    }
 
-        // first loop: q = g; alpha_i = rho_i s_i^T q; q -= alpha_i y_i (newest first)
+    // First loop of the two-loop recursion: q = g; alpha_i = rho_i s_i^T q;
+    // q -= alpha_i y_i (newest first).  q is left in Dv.
+    __device__ void first_loop()
+    {
+        const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x;
         for (int e = tid; e < N3; e += NT) Dv[e] = g[e];
         for (int q = 0; q < count; ++q) {
             const int i = (head - 1 - q + M) % M;
-            const T* S = vec_ptr(gd, smem, slot, V_SBASE + i);
-            const T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + i);
+            const T* S = hist(V_SBASE + i);
+            const T* Y = hist(V_SBASE + M + i);
             T s[1] = {T(0)};
             for (int e = tid; e < N3; e += NT) s[0] += S[e] * Dv[e];
             block_sum<T, 1>(s, smem, [=](CellShared* c) { c->alpha[i] = c->rho[i] * c->out[0]; });
             const T al = (T)sh->alpha[i];
             for (int e = tid; e < N3; e += NT) Dv[e] -= al * Y[e];
         }
-        // r = H0 q through the dense inverse (contract_simt syncs before reading q)
-        contract_simt(tp, Dv, GCv, TRIv);
-        // second loop: beta = rho_i y_i^T r; r += s_i (alpha_i - beta) (oldest first)
+        __syncthreads();
+    }
+
+    // Second loop (oldest first) on r = H0 q held in GCv: beta = rho_i y_i^T r;
+    // r += s_i (alpha_i - beta); then d = -r into Dv and gdv = g^T d.
+    __device__ void second_loop()
+    {
+        const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x;
         for (int q = count - 1; q >= 0; --q) {
             const int i = (head - 1 - q + M) % M;
-            const T* S = vec_ptr(gd, smem, slot, V_SBASE + i);
-            const T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + i);
+            const T* S = hist(V_SBASE + i);
+            const T* Y = hist(V_SBASE + M + i);
             T s[1] = {T(0)};
             for (int e = tid; e < N3; e += NT) s[0] += Y[e] * GCv[e];
             block_sum<T, 1>(s, smem, [=](CellShared* c) { c->out[1] = c->alpha[i] - c->rho[i] * c->out[0]; });
             const T coef = (T)sh->out[1];
             for (int e = tid; e < N3; e += NT) GCv[e] += S[e] * coef;
         }
-        double gdv;
-        {
-            T s[1] = {T(0)};
-            for (int e = tid; e < N3; e += NT) {
-                const T dv = -GCv[e];
-                Dv[e] = dv;
-                s[0] += g[e] * dv;
-            }
-            block_sum<T, 1>(s, smem);
-            gdv = sh->out[0];
-        }
-        if (!(gdv < 0.0)) {
-            // not a descent direction: drop the history, d = -H~^-1 g
-            count = 0;
-            contract_simt(tp, g, GCv, TRIv);
-            T s[1] = {T(0)};
-            for (int e = tid; e < N3; e += NT) {
-                const T dv = -GCv[e];
-                Dv[e] = dv;
-                s[0] += g[e] * dv;
-            }
-            block_sum<T, 1>(s, smem);
-            gdv = sh->out[0];
-        }
+        negate_direction();
+    }
 
-        // backtracking line search alpha = 1, 1/2, ... (Armijo; the FP32 path widens the
-        // bound by a multiple of the estimated rounding error of g)
+    // d = -GCv into Dv, gdv = g^T d.
+    __device__ void negate_direction()
+    {
+        const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x;
+        T s[1] = {T(0)};
+        for (int e = tid; e < N3; e += NT) {
+            const T dv = -GCv[e];
+            Dv[e] = dv;
+            s[0] += g[e] * dv;
+        }
+        block_sum<T, 1>(s, smem);
+        gdv = sh->out[0];
+    }
+
+    __device__ bool descent() const { return gdv < 0.0; }
+
+    // Backtracking line search alpha = 1, 1/2, ... with the Armijo test (the FP32
+    // path widens the bound by a multiple of the estimated rounding error of g),
+    // history update and acceptance.  Returns false when no step length passed.
+    __device__ bool line_search_update()
+    {
+        const TopoDev<T>& T_ = tp();
+        const int N3 = 3 * T_.n_pad, tid = threadIdx.x, NT = blockDim.x;
+        const double c1 = a->p.c1, c2 = a->p.c2, anoise = a->p.armijo_noise;
         double alpha = 1.0;
         bool accepted = false;
-        for (int hv = 0; hv <= a.p.max_halvings; ++hv) {
+        for (int hv = 0; hv <= a->p.max_halvings; ++hv) {
             const T al = (T)alpha;
             for (int e = tid; e < N3; e += NT) ut[e] = u[e] + al * Dv[e];
             __syncthreads();
-            evaluate(tp, XN, ut, UYv, gt, GCv, TRIv, WRv, Vn, smem);
+            evaluate(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, Vn, smem);
             ++evals;
             if (tid == 0) {
                 const bool ok = !sh->bad && sh->E <= E + c1 * alpha * gdv + anoise * (sh->noise + noiseE);
-                sh->accept = a.p.fixed_alpha || ok;
+                sh->accept = a->p.fixed_alpha || ok;
             }
             __syncthreads();
             if (sh->accept) {
@@ -807,7 +853,7 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
         }
         if (!accepted) {
             status = NPFEM_CELL_LINESEARCH_FAIL;
-            break;
+            return false;
         }
         // history pair (s, y) = (x_{k+1} - x_k, grad_{k+1} - grad_k), kept when the
         // curvature condition holds and s^T y > 0
@@ -821,13 +867,14 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
                 acc[3] += gt[e] * Dv[e];
             }
             const int hd = head;
+            const double gd0 = gdv;
             block_sum<T, 4>(acc, smem, [=](CellShared* c) {
-                c->push = c->out[3] >= c2 * gdv && c->out[0] > 1e-12 * sqrt(c->out[1] * c->out[2]);
+                c->push = c->out[3] >= c2 * gd0 && c->out[0] > 1e-12 * sqrt(c->out[1] * c->out[2]);
                 if (c->push) c->rho[hd] = 1.0 / c->out[0];
             });
             if (sh->push) {
-                T* S = vec_ptr(gd, smem, slot, V_SBASE + head);
-                T* Y = vec_ptr(gd, smem, slot, V_SBASE + M + head);
+                T* S = hist(V_SBASE + head);
+                T* Y = hist(V_SBASE + M + head);
                 for (int e = tid; e < N3; e += NT) {
                     S[e] = ut[e] - u[e];
                     Y[e] = gt[e] - g[e];
@@ -836,8 +883,8 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
                 count = count < M ? count + 1 : M;
             }
         }
-        T* tp1 = u; u = ut; ut = tp1;
-        T* tp2 = g; g = gt; gt = tp2;
+        T* t1 = u; u = ut; ut = t1;
+        T* t2 = g; g = gt; gt = t2;
         E = sh->E;
         noiseE = sh->noise;
         res = sh->res;
@@ -845,127 +892,485 @@ __device__ void solve_cell(const LaunchArgs<T>& a, const GroupDesc<T>& gd, long 
         ++iters;
         nonfinite = sh->bad || !isfinite(sh->E) || !isfinite(sh->res);
         __syncthreads();
+        return true;
     }
-    if (nonfinite) status = NPFEM_CELL_NONFINITE;
 
-    // ---- v_{n+1} = (x_{n+1} - x_n)/h and post-convergence dissipation (Sec. 2.1.4)
-    const T inv_h = T(1) / h;
-    Acc<T> ps[16];
-    if (!nonfinite) {
+    // v_{n+1} = (x_{n+1} - x_n)/h and post-convergence dissipation (Sec. 2.1.4);
+    // writes x, v and the cell's statistics.
+    __device__ void finish()
+    {
+        const TopoDev<T>& T_ = tp();
+        const int n = T_.n, np = T_.n_pad, tid = threadIdx.x, NT = blockDim.x;
+        if (nonfinite) status = NPFEM_CELL_NONFINITE;
+        const T inv_h = T(1) / T_.h;
+        Acc<T> ps[16];
+        if (!nonfinite) {
+            for (int i = tid; i < n; i += NT) {
+                const T m = __ldg(&T_.mass[i]);
+                T xr[3], vr[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    xr[c] = XN[c * np + i] + u[c * np + i];
+                    vr[c] = u[c * np + i] * inv_h;
+                }
+                ps[0].add(m);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    ps[1 + c].add(m * xr[c]);
+                    ps[4 + c].add(m * vr[c]);
+                }
+                ps[7].add(m * (xr[1] * vr[2] - xr[2] * vr[1]));
+                ps[8].add(m * (xr[2] * vr[0] - xr[0] * vr[2]));
+                ps[9].add(m * (xr[0] * vr[1] - xr[1] * vr[0]));
+                ps[10].add(m * xr[0] * xr[0]);
+                ps[11].add(m * xr[1] * xr[1]);
+                ps[12].add(m * xr[2] * xr[2]);
+                ps[13].add(m * xr[0] * xr[1]);
+                ps[14].add(m * xr[0] * xr[2]);
+                ps[15].add(m * xr[1] * xr[2]);
+            }
+        }
+        const bool nf = nonfinite;
+        block_reduce<T, 16>(ps, smem, [=](CellShared* s) {
+            double* o = s->out;
+            double* P = s->post;
+            for (int q = 0; q < 9; ++q) P[q] = 0.0;
+            if (nf) return;
+            const double Mt = o[0];
+            double xc[3], vc[3];
+            for (int c = 0; c < 3; ++c) {
+                xc[c] = o[1 + c] / Mt;
+                vc[c] = o[4 + c] / Mt;
+            }
+            // angular momentum and inertia tensor about the centre of mass
+            const double L0 = o[7] - Mt * (xc[1] * vc[2] - xc[2] * vc[1]);
+            const double L1 = o[8] - Mt * (xc[2] * vc[0] - xc[0] * vc[2]);
+            const double L2 = o[9] - Mt * (xc[0] * vc[1] - xc[1] * vc[0]);
+            const double Sxx = o[10] - Mt * xc[0] * xc[0], Syy = o[11] - Mt * xc[1] * xc[1],
+                         Szz = o[12] - Mt * xc[2] * xc[2];
+            const double Sxy = o[13] - Mt * xc[0] * xc[1], Sxz = o[14] - Mt * xc[0] * xc[2],
+                         Syz = o[15] - Mt * xc[1] * xc[2];
+            const double I00 = Syy + Szz, I11 = Sxx + Szz, I22 = Sxx + Syy;
+            const double I01 = -Sxy, I02 = -Sxz, I12 = -Syz;
+            const double c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
+            const double c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
+            const double det = I00 * c00 + I01 * c01 + I02 * c02;
+            for (int c = 0; c < 3; ++c) {
+                P[c] = xc[c];
+                P[3 + c] = vc[c];
+            }
+            P[6] = (c00 * L0 + c01 * L1 + c02 * L2) / det;
+            P[7] = (c01 * L0 + c11 * L1 + c12 * L2) / det;
+            P[8] = (c02 * L0 + c12 * L1 + c22 * L2) / det;
+        });
+        const T xc[3] = {(T)sh->post[0], (T)sh->post[1], (T)sh->post[2]};
+        const T vc[3] = {(T)sh->post[3], (T)sh->post[4], (T)sh->post[5]};
+        const T w[3] = {(T)sh->post[6], (T)sh->post[7], (T)sh->post[8]};
+        const T kap = T_.kappa;
+        T* x = a->x + so;
+        T* v = a->v + so;
         for (int i = tid; i < n; i += NT) {
-            const T m = __ldg(&tp.mass[i]);
-            T xr[3], vr[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                xr[c] = XN[c * np + i] + u[c * np + i];
-                vr[c] = u[c * np + i] * inv_h;
+            if (nonfinite) {
+                for (int c = 0; c < 3; ++c) v[c * n + i] = T(0);
+                continue;
             }
-            ps[0].add(m);
-#pragma unroll
+            T r[3];
+            for (int c = 0; c < 3; ++c) r[c] = XN[c * np + i] + u[c * np + i] - xc[c];
+            const T wr[3] = {w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2], w[0] * r[1] - w[1] * r[0]};
             for (int c = 0; c < 3; ++c) {
-                ps[1 + c].add(m * xr[c]);
-                ps[4 + c].add(m * vr[c]);
+                const T uc = u[c * np + i];
+                const T vv = uc * inv_h;
+                v[c * n + i] = vv + kap * (vc[c] + wr[c] - vv);
+                x[c * n + i] = x[c * n + i] + uc;
             }
-            ps[7].add(m * (xr[1] * vr[2] - xr[2] * vr[1]));
-            ps[8].add(m * (xr[2] * vr[0] - xr[0] * vr[2]));
-            ps[9].add(m * (xr[0] * vr[1] - xr[1] * vr[0]));
-            ps[10].add(m * xr[0] * xr[0]);
-            ps[11].add(m * xr[1] * xr[1]);
-            ps[12].add(m * xr[2] * xr[2]);
-            ps[13].add(m * xr[0] * xr[1]);
-            ps[14].add(m * xr[0] * xr[2]);
-            ps[15].add(m * xr[1] * xr[2]);
         }
+        if (tid == 0 && a->stats) {
+            npfem_cell_stats st;
+            st.iterations = iters;
+            st.evaluations = evals;
+            st.status = status;
+            st.residual = (float)res;
+            st.objective = E;
+            st.volume = Vlast;
+            a->stats[item] = st;
+        }
+        __syncthreads();
     }
-    const bool nf = nonfinite;
-    block_reduce<T, 16>(ps, smem, [=](CellShared* s) {
-        double* o = s->out;
-        double* P = s->post;
-        for (int q = 0; q < 9; ++q) P[q] = 0.0;
-        if (nf) return;
-        const double Mt = o[0];
-        double xc[3], vc[3];
-        for (int c = 0; c < 3; ++c) {
-            xc[c] = o[1 + c] / Mt;
-            vc[c] = o[4 + c] / Mt;
-        }
-        // angular momentum and inertia tensor about the centre of mass
-        const double L0 = o[7] - Mt * (xc[1] * vc[2] - xc[2] * vc[1]);
-        const double L1 = o[8] - Mt * (xc[2] * vc[0] - xc[0] * vc[2]);
-        const double L2 = o[9] - Mt * (xc[0] * vc[1] - xc[1] * vc[0]);
-        const double Sxx = o[10] - Mt * xc[0] * xc[0], Syy = o[11] - Mt * xc[1] * xc[1], Szz = o[12] - Mt * xc[2] * xc[2];
-        const double Sxy = o[13] - Mt * xc[0] * xc[1], Sxz = o[14] - Mt * xc[0] * xc[2], Syz = o[15] - Mt * xc[1] * xc[2];
-        const double I00 = Syy + Szz, I11 = Sxx + Szz, I22 = Sxx + Syy;
-        const double I01 = -Sxy, I02 = -Sxz, I12 = -Syz;
-        const double c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
-        const double c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
-        const double det = I00 * c00 + I01 * c01 + I02 * c02;
-        for (int c = 0; c < 3; ++c) {
-            P[c] = xc[c];
-            P[3 + c] = vc[c];
-        }
-        P[6] = (c00 * L0 + c01 * L1 + c02 * L2) / det;
-        P[7] = (c01 * L0 + c11 * L1 + c12 * L2) / det;
-        P[8] = (c02 * L0 + c12 * L1 + c22 * L2) / det;
-    });
-    const T xc[3] = {(T)sh->post[0], (T)sh->post[1], (T)sh->post[2]};
-    const T vc[3] = {(T)sh->post[3], (T)sh->post[4], (T)sh->post[5]};
-    const T w[3] = {(T)sh->post[6], (T)sh->post[7], (T)sh->post[8]};
-    const T kap = tp.kappa;
-    T* x = a.x + so;
-    T* v = a.v + so;
-    for (int i = tid; i < n; i += NT) {
-        if (nonfinite) {
-            for (int c = 0; c < 3; ++c) v[c * n + i] = T(0);
-            continue;
-        }
-        T r[3];
-        for (int c = 0; c < 3; ++c) r[c] = XN[c * np + i] + u[c * np + i] - xc[c];
-        const T wr[3] = {w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2], w[0] * r[1] - w[1] * r[0]};
-        for (int c = 0; c < 3; ++c) {
-            const T uc = u[c * np + i];
-            const T vv = uc * inv_h;
-            v[c * n + i] = vv + kap * (vc[c] + wr[c] - vv);
-            x[c * n + i] = x[c * n + i] + uc;
-        }
-    }
-    if (tid == 0 && a.stats) {
-        npfem_cell_stats st;
-        st.iterations = iters;
-        st.evaluations = evals;
-        st.status = status;
-        st.residual = (float)res;
-        st.objective = E;
-        st.volume = Vlast;
-        a.stats[item] = st;
-    }
+};
+
+// Next work item of the launch (block-uniform), or -1.
+template <typename T>
+__device__ __forceinline__ long long next_item(const LaunchArgs<T>& a, unsigned char* smem)
+{
+    CellShared* sh = cell_shared(smem);
+    if (threadIdx.x == 0) sh->item = (long long)atomicAdd(&a.work[0], 1u);
     __syncthreads();
+    const long long it = sh->item;
+    __syncthreads();
+    return it < a.total_cells ? it : -1;
+}
+
+// The last block to finish resets the work counters for the next launch.
+__device__ __forceinline__ void release_counters(unsigned int* work)
+{
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&work[1], 1u);
+        if (prev == gridDim.x * gridDim.y * gridDim.z - 1) {
+            atomicExch(&work[0], 0u);
+            atomicExch(&work[1], 0u);
+        }
+    }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(512, 1) cell_kernel(const __grid_constant__ LaunchArgs<T> a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_item;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    CellSolver<T> S;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&a.work[0], 1u);
-        __syncthreads();
-        const long long item = s_item;
-        __syncthreads();
-        if (item >= a.total_cells) break;
+        const long long item = next_item(a, smem);
+        if (item < 0) break;
         int gi = 0;
         while (gi + 1 < a.n_groups && item >= a.g[gi + 1].cell_begin) ++gi;
-        solve_cell<T>(a, a.g[gi], item - a.g[gi].cell_begin, item, smem);
-    }
-    // the last block to finish resets the work counters for the next launch
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&a.work[1], 1u);
-        if (prev == gridDim.x - 1) {
-            atomicExch(&a.work[0], 0u);
-            atomicExch(&a.work[1], 0u);
+        S.bind(a, a.g[gi], smem);
+        if (!S.begin(item - a.g[gi].cell_begin, item)) continue;
+        const TopoDev<T>& tp = a.g[gi].topo;
+        while (S.wants_direction()) {
+            S.first_loop();
+            contract_simt(tp, S.Dv, S.GCv, S.TRIv);  // r = H0 q
+            S.second_loop();
+            if (!S.descent()) {
+                // not a descent direction: drop the history, d = -H~^-1 g
+                S.count = 0;
+                contract_simt(tp, S.g, S.GCv, S.TRIv);
+                S.negate_direction();
+            }
+            if (!S.line_search_update()) break;
         }
+        S.finish();
     }
+    release_counters(a.work);
+}
+
+// ---------------------------------------------------------------------------------
+// Tensor-core contraction: a cluster of ceil(n / 128) blocks, one block per SM, each
+// holding rows [128 r, 128 r + 128) of A^-1 (BF16) in tensor memory for the whole
+// launch.  A "round" applies A^-1 to the current request of every block of the
+// cluster at once:
+//   local work  -> each block with a request writes its vector (BF16) into row
+//                  3 r + c of the B operand of every block of the cluster (DSMEM);
+//   barrier     -> every block issues ceil(n/16) tcgen05.mma (M 128, N 16/32, K 16,
+//                  A from TMEM, B from shared memory, FP32 accumulate in TMEM),
+//                  reads its 128 result rows and writes them into the requesting
+//                  blocks' contraction vectors (DSMEM);
+//   barrier     -> results are in place.
+// Blocks without work still take part until every block of the cluster is idle, so
+// all blocks pass the same sequence of cluster barriers.
+// ---------------------------------------------------------------------------------
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cta_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t map_rank(uint32_t local, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_remote_v4(uint32_t addr, uint4 v)
+{
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_remote_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_remote_u32(uint32_t addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const unsigned short l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const unsigned short h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return ((uint32_t)h << 16) | l;
+}
+
+// byte offset of B element (row nrow, column k) in the no-swizzle K-major layout:
+// 8 x 8 core matrices of 128 bytes, K-adjacent core matrices 128 bytes apart
+// (leading byte offset), row groups (Kpad / 8) * 128 bytes apart (stride byte offset)
+__device__ __forceinline__ uint32_t b_offset(int nrow, int k, int kpad)
+{
+    return (uint32_t)(((nrow >> 3) * (kpad >> 3) + (k >> 3)) * 128 + (nrow & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; no swizzle, base offset 0
+    return d;
+}
+
+template <int NCOL>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[NCOL])
+{
+    uint32_t r[NCOL];
+    if constexpr (NCOL == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+            "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+}  // namespace tc
+
+// Writes BF16(src) (3 rows of the cell, zero beyond n) into rows 3 rank + c of the B
+// operand of every block in the cluster.  If with_residual, writes instead the
+// refinement residual e = src - H~ r (H~ = ms M + L, sparse FP32) for r = R.
+template <typename T>
+__device__ void tc_post(const TopoDev<T>& tp, const T* src, const T* R, bool with_residual, unsigned char* bbuf,
+                        uint32_t rank, uint32_t cs)
+{
+    const int n = tp.n, np = tp.n_pad, kpad = tp.kpad, tid = threadIdx.x, NT = blockDim.x;
+    const int chunks = 3 * (kpad >> 3);
+    const float ms = (float)(tp.inertia_scale * tp.inv_h2);
+    const uint32_t local = tc::smem_addr(bbuf);
+    for (int q = tid; q < chunks; q += NT) {
+        const int c = q / (kpad >> 3), kb = q - c * (kpad >> 3);
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = 8 * kb + u;
+            float val = 0.f;
+            if (k < n) {
+                val = (float)src[c * np + k];
+                if (with_residual) {
+                    float hr = ms * (float)__ldg(&tp.mass[k]) * (float)R[c * np + k];
+                    const int b0 = __ldg(&tp.h_ptr[k]), b1 = __ldg(&tp.h_ptr[k + 1]);
+                    for (int p = b0; p < b1; ++p) hr += __ldg(&tp.h_val[p]) * (float)R[c * np + __ldg(&tp.h_idx[p])];
+                    val -= hr;
+                }
+            }
+            v[u] = val;
+        }
+        const uint4 w = make_uint4(tc::pack_bf16(v[0], v[1]), tc::pack_bf16(v[2], v[3]), tc::pack_bf16(v[4], v[5]),
+                                   tc::pack_bf16(v[6], v[7]));
+        const uint32_t off = tc::b_offset(3 * (int)rank + c, 8 * kb, kpad);
+        for (uint32_t d = 0; d < cs; ++d) tc::st_remote_v4(tc::map_rank(local + off, d), w);
+    }
+}
+
+enum TcPhase { PH_NONE = 0, PH_DIR1, PH_DIR2, PH_FB1, PH_FB2 };
+
+template <typename T, int NCOL>
+__global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__ LaunchArgs<T> a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const GroupDesc<T>& gd = a.g[0];
+    const TopoDev<T>& tp = gd.topo;
+    CellShared* sh = cell_shared(smem);
+    unsigned char* bbuf = smem + kFixedSmem;  // B operand: NCOL rows x kpad BF16
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = tc::cta_rank(), cs = (uint32_t)a.p.cluster;
+    const int n = tp.n, np = tp.n_pad, kpad = tp.kpad;
+    const uint32_t acols = (uint32_t)(kpad >> 1);
+    const uint32_t dcol = (acols + 31u) & ~31u;
+
+    // ---- set-up: zero B, flags, TMEM allocation, A^-1 rows of this block into TMEM
+    for (int q = tid; q < NCOL * kpad / 8; q += blockDim.x) reinterpret_cast<uint4*>(bbuf)[q] = make_uint4(0, 0, 0, 0);
+    if (tid < 16) sh->need[tid] = 0u;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&sh->mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+            tc::smem_addr(&sh->taddr)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = sh->taddr;
+    if (warp < 4) {
+        const int row = 128 * (int)rank + 32 * warp + lane;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(tp.ainv_lp) + (size_t)row * (kpad >> 1);
+        for (int c0 = 0; c0 < (int)acols; c0 += 8) {
+            uint32_t r[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] = __ldg(&src[c0 + j]);
+            const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta), "r"(r[0]),
+                         "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]));
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc::cluster_sync();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCOL >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t lbo = 128u, sbo = (uint32_t)(kpad >> 3) * 128u;
+    const uint32_t bbase = tc::smem_addr(bbuf);
+    const bool refine = a.p.refine != 0;
+
+    CellSolver<T> S;
+    S.bind(a, gd, smem);
+    int phase = PH_NONE;
+    bool have_result = false, exhausted = false;
+    uint32_t round = 0;
+    for (;;) {
+        // ---- local work up to the next request (or idle)
+        bool need = false;
+        for (;;) {
+            if (phase == PH_NONE) {
+                const long long item = exhausted ? -1 : next_item(a, smem);
+                if (item < 0) {
+                    exhausted = true;
+                    break;
+                }
+                S.begin(item, item);
+            } else if (have_result) {
+                have_result = false;
+                if ((phase == PH_DIR1 || phase == PH_FB1) && refine) {
+                    // keep r1, request A^-1 (src - H~ r1)
+                    const int N3 = 3 * np;
+                    for (int e = tid; e < N3; e += blockDim.x) S.ut[e] = S.GCv[e];
+                    __syncthreads();
+                    tc_post(tp, phase == PH_DIR1 ? S.Dv : S.g, S.GCv, true, bbuf, rank, cs);
+                    phase = phase == PH_DIR1 ? PH_DIR2 : PH_FB2;
+                    need = true;
+                    break;
+                }
+                if (phase == PH_DIR2 || phase == PH_FB2) {
+                    const int N3 = 3 * np;
+                    for (int e = tid; e < N3; e += blockDim.x) S.GCv[e] += S.ut[e];
+                    __syncthreads();
+                }
+                if (phase == PH_DIR1 || phase == PH_DIR2) {
+                    S.second_loop();
+                    if (!S.descent()) {
+                        S.count = 0;
+                        tc_post(tp, S.g, S.GCv, false, bbuf, rank, cs);
+                        phase = PH_FB1;
+                        need = true;
+                        break;
+                    }
+                } else {
+                    S.negate_direction();
+                }
+                if (!S.line_search_update()) {
+                    S.finish();
+                    phase = PH_NONE;
+                    continue;
+                }
+            }
+            if (!S.wants_direction()) {
+                S.finish();
+                phase = PH_NONE;
+                continue;
+            }
+            S.first_loop();
+            tc_post(tp, S.Dv, S.GCv, false, bbuf, rank, cs);
+            phase = PH_DIR1;
+            need = true;
+            break;
+        }
+        // announce the request flag to every block of the cluster
+        if (tid < (int)cs) tc::st_remote_u32(tc::map_rank(tc::smem_addr(&sh->need[rank]), (uint32_t)tid), need ? 1u : 0u);
+        asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+        tc::cluster_sync();
+        uint32_t any = 0;
+        for (uint32_t d = 0; d < cs; ++d) any |= sh->need[d];
+        if (!any) break;
+
+        // ---- the round: MMAs on this block's row block for every request
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < (kpad >> 4); ++ks) {
+                const uint64_t bd = tc::smem_desc(bbase + (uint32_t)ks * 256u, lbo, sbo);
+                const uint32_t ta = tbase + (uint32_t)(ks * 8);
+                const uint32_t acc = ks > 0;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tbase + dcol),
+                    "r"(ta), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc::smem_addr(&sh->mbar)));
+        }
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 22) && !done; ++it) {
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                : "=r"(done)
+                : "r"(tc::smem_addr(&sh->mbar)), "r"(round & 1u));
+        }
+        if (!done && tid == 0) atomicExch(&a.work[2], 1u);  // reported to the host; results invalid
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (warp < 4) {
+            float dv[NCOL];
+            tc::tmem_ld<NCOL>(tbase + ((uint32_t)(32 * warp) << 16) + dcol, dv);
+            const int row = 128 * (int)rank + 32 * warp + lane;
+            if (row < n) {
+#pragma unroll
+                for (int d = 0; d < NCOL / 3 && d < 8; ++d) {
+                    if (d >= (int)cs || !sh->need[d]) continue;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const uint32_t loc = tc::smem_addr(S.GCv + c * np + row);
+                        tc::st_remote_f32(tc::map_rank(loc, (uint32_t)d), dv[3 * d + c]);
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        tc::cluster_sync();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        have_result = need;
+        ++round;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc::cluster_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+    release_counters(a.work);
 }
 
 }  // namespace
@@ -980,6 +1385,43 @@ template <typename T>
 cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s)
 {
     cell_kernel<T><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Cluster launch of the tensor-core kernel for one mesh group; returns the grid in
+// *grid_out (cluster size x co-resident clusters, capped by the cell count).
+cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, int smem, cudaStream_t s,
+                            int* grid_out)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const bool wide = cluster * 3 > 16;
+    auto kern32 = cell_kernel_tc<float, 32>;
+    auto kern16 = cell_kernel_tc<float, 16>;
+    cudaError_t e = wide ? cudaFuncSetAttribute(kern32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                         : cudaFuncSetAttribute(kern16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int nclusters = 0;
+    cfg.gridDim = dim3(cluster);
+    e = wide ? cudaOccupancyMaxActiveClusters(&nclusters, kern32, &cfg)
+             : cudaOccupancyMaxActiveClusters(&nclusters, kern16, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nclusters < 1) return cudaErrorInvalidConfiguration;
+    long long want = (a.total_cells + cluster - 1) / cluster;
+    if (want > nclusters) want = nclusters;
+    cfg.gridDim = dim3((unsigned)(want * cluster));
+    *grid_out = (int)(want * cluster);
+    e = wide ? cudaLaunchKernelEx(&cfg, kern32, a) : cudaLaunchKernelEx(&cfg, kern16, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ class Material(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("lbfgs_m", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("c1", C.c_double), ("c2", C.c_double), ("max_halvings", C.c_int32), ("fixed_alpha", C.c_int32),
-                ("equal_mass", C.c_int32), ("armijo_noise", C.c_double)]
+                ("equal_mass", C.c_int32), ("armijo_noise", C.c_double), ("refine", C.c_int32)]
 
 
 class CellStats(C.Structure):
@@ -47,7 +47,8 @@ CELL_STATS_DTYPE = np.dtype([("iterations", "<i4"), ("evaluations", "<i4"), ("st
 
 _lib = None
 EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", "npfem_step_host", "npfem_eval",
-           "npfem_get_inverse", "npfem_get_rest_info", "npfem_last_error", "npfem_step_static")
+           "npfem_get_inverse", "npfem_get_rest_info", "npfem_last_error", "npfem_step_static",
+           "npfem_check_device")
 
 
 def lib_path() -> str:
@@ -71,6 +72,7 @@ def lib():
         L.npfem_eval.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.npfem_get_inverse.argtypes = [vp, vp]
         L.npfem_get_rest_info.argtypes = [vp, vp, vp]
+        L.npfem_check_device.argtypes = [vp]
         L.npfem_last_error.restype = C.c_char_p
         L.npfem_last_error.argtypes = []
         for name in EXPORTS:
@@ -147,6 +149,10 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+    def check_device(self):
+        """Raises NpfemError(-5) if a bounded device wait of a previous step gave up."""
+        _check(lib().npfem_check_device(self._h))
 
     def inverse(self) -> np.ndarray:
         out = np.zeros((self.n, self.n))

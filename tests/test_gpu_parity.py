@@ -242,3 +242,50 @@ def test_full_size_sampled(npfem):
     sample = np.random.default_rng(0).choice(16384, 8, replace=False)
     xo, vo, _ = oracle_steps(m, p["x"][sample], p["v"][sample], p["f"][sample], tol=1e-10, max_iter=200)
     assert max_rel_disp(xg[sample], xo, m.lbar) <= 1e-5 + fp32_store_allowance(p["x"], m.lbar)
+
+
+# ---------------------------------------------------------------------------------
+# BF16 tensor-core contraction (A^-1 resident in tensor memory across a cluster):
+# the direction changes only through H0, so the converged step must still meet the
+# FP32 parity tolerance at the same residual tolerance.
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("n_verts,cells,refine", [(642, 13, 1), (642, 8, 0), (258, 7, 1)])
+def test_step_bf16_tensor_core(npfem, n_verts, cells, refine):
+    h = make_handle(npfem, n_verts, "bf16", tol=1e-6, refine=refine)
+    m, _, _ = oracle_model(n_verts)
+    p = population32(n_verts, cells, seed=40 + n_verts, forces="shear", noise_pN=0.5)
+    xo, vo, st = oracle_steps(m, p["x"], p["v"], p["f"], tol=1e-10, max_iter=200)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    h.check_device()
+    assert (sg["status"] == 0).all(), sg
+    assert (sg["residual"] <= 1e-6).all()
+    assert max_rel_disp(xg, xo, m.lbar) <= 1e-5 + fp32_store_allowance(p["x"], m.lbar)
+    assert max_rel_disp(DT * vg, DT * vo, m.lbar) <= 1e-5
+
+
+def test_bf16_iterations_close_to_fp32(npfem):
+    p = population32(642, 64, seed=50, forces="shear", noise_pN=0.5)
+    out = {}
+    for prec in ("fp32", "bf16"):
+        h = make_handle(npfem, 642, prec, tol=1e-6)
+        _, _, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+        out[prec] = sg["iterations"].mean()
+    assert out["bf16"] <= out["fp32"] + 1.0, out
+
+
+def test_bf16_full_size_sampled(npfem):
+    h = make_handle(npfem, 642, "bf16", tol=1e-6)
+    m, _, _ = oracle_model(642)
+    p = population32(642, 16384, seed=3, forces="shear", gamma_fixed=1000.0, noise_pN=2.0)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    h.check_device()
+    assert (sg["status"] == 0).all() and (sg["residual"] <= 1e-6).all()
+    sample = np.random.default_rng(1).choice(16384, 8, replace=False)
+    xo, vo, _ = oracle_steps(m, p["x"][sample], p["v"][sample], p["f"][sample], tol=1e-10, max_iter=200)
+    assert max_rel_disp(xg[sample], xo, m.lbar) <= 1e-5 + fp32_store_allowance(p["x"], m.lbar)
+
+
+def test_tf32_is_rejected(npfem):
+    with pytest.raises(npfem.NpfemError) as e:
+        make_handle(npfem, 258, "tf32")
+    assert e.value.code == -1
