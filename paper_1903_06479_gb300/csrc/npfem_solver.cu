@@ -65,7 +65,7 @@ struct Acc {
 // Per-cell scalars shared by the block (after the 8 KB of reduction partials).
 struct CellShared {
     double out[16];          // results of the last block_reduce
-    double V, E, Ein, Earea, Esk, Ebend, Evol, res, noise;
+    double V, Vn, E, Ein, Earea, Esk, Ebend, Evol, res, noise;
     double rho[kMaxHistory];
     double alpha[kMaxHistory];
     double post[12];         // centre of mass, its velocity, angular velocity
@@ -309,7 +309,9 @@ __device__ void volume_at_xn(const TopoDev<T>& tp, const T* XN, unsigned char* s
 // incidence) and computes the bending residual w_i r_i into WR; pass 3 gathers the
 // bending gradient from the neighbours' WR (transposed cotangent weights) and adds
 // the volume and inertia terms.  Every vertex is written by one thread only.
-template <typename T>
+// With kFirst, the same triangle pass also accumulates V(x_n) (left in sh->Vn) and
+// Vn is ignored.
+template <typename T, bool kFirst = false>
 __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T* UY, T* Gout, T* GC, T* TRI, T* WR,
                          double Vn, unsigned char* smem)
 {
@@ -317,7 +319,7 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
     CellShared* sh = cell_shared(smem);
     const T Cs = tp.C, Bs = tp.B, Ds = tp.Dsk;
     const T sixth = T(1) / T(6);
-    Acc<T> ce[4];  // area, Skalak, bending energies; 6 dV
+    Acc<T> ce[5];  // area, Skalak, bending energies; 6 dV; 6 V(x_n) (first evaluation only)
     T pl[3] = {T(0), T(0), T(0)};  // |grad C|^2, rounding estimate, degenerate count
 
     // ---- pass 1: triangles
@@ -347,6 +349,9 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
             e2[c] = E2[c] + d2[c];
         }
         T* out = TRI + 9 * t;
+        if (kFirst)
+            ce[4].add(Xi[0] * (E1[1] * E2[2] - E1[2] * E2[1]) + Xi[1] * (E1[2] * E2[0] - E1[0] * E2[2]) +
+                      Xi[2] * (E1[0] * E2[1] - E1[1] * E2[0]));
         // F = D_s D_m^{-1} (3 x 2), columns F0, F1
         T F0[3], F1[3];
 #pragma unroll
@@ -498,17 +503,19 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
         for (int c = 0; c < 3; ++c) WR[c * np + i] = w * r[c];
     }
     const double kvol = (double)tp.kvol, V0 = tp.V0;
-    block_reduce_cp<T, 4, 3>(ce, pl, smem, [=](CellShared* s) {
+    block_reduce_cp<T, 5, 3>(ce, pl, smem, [=](CellShared* s) {
         s->Earea = s->out[0];
         s->Esk = s->out[1];
         s->Ebend = s->out[2];
-        s->V = Vn + s->out[3] / 6.0;
+        const double vn = kFirst ? s->out[4] / 6.0 : Vn;
+        s->Vn = vn;
+        s->V = vn + s->out[3] / 6.0;
         const double Cv = s->V - V0;
-        const T inv = T(1) / (T)s->out[4];
+        const T inv = T(1) / (T)s->out[5];
         s->Evol = 0.5 * kvol * Cv * Cv * (double)inv;
         s->volc = kvol * Cv * (double)inv;
-        s->noise = s->out[5];
-        s->bad = s->out[6] != 0.0;
+        s->noise = s->out[6];
+        s->bad = s->out[7] != 0.0;
     });
     const T volc = (T)sh->volc;
 
@@ -730,9 +737,8 @@ struct CellSolver {
             u[e] = eval_mode ? T(0) : uy;
         }
         __syncthreads();
-        volume_at_xn(T_, XN, smem);
-        Vn = sh->V;
-        evaluate(T_, XN, u, UYv, g, GCv, TRIv, WRv, Vn, smem);
+        evaluate<T, true>(T_, XN, u, UYv, g, GCv, TRIv, WRv, 0.0, smem);
+        Vn = sh->Vn;
         evals = 1;
         iters = 0;
         status = NPFEM_CELL_OK;
@@ -1163,31 +1169,48 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[NCOL])
 // Writes BF16(src) (3 rows of the cell, zero beyond n) into rows 3 rank + c of the B
 // operand of every block in the cluster.  If with_residual, writes instead the
 // refinement residual e = src - H~ r (H~ = ms M + L, sparse FP32) for r = R.
+// tmp: 3 x n_pad scratch (the bending buffer, idle outside the evaluation).
 template <typename T>
 __device__ void tc_post(const TopoDev<T>& tp, const T* src, const T* R, bool with_residual, unsigned char* bbuf,
-                        uint32_t rank, uint32_t cs)
+                        uint32_t rank, uint32_t cs, T* tmp)
 {
     const int n = tp.n, np = tp.n_pad, kpad = tp.kpad, tid = threadIdx.x, NT = blockDim.x;
     const int chunks = 3 * (kpad >> 3);
-    const float ms = (float)(tp.inertia_scale * tp.inv_h2);
     const uint32_t local = tc::smem_addr(bbuf);
+    if (with_residual) {
+        // e = src - H~ R, one row (three components) per thread
+        const T ms = tp.inertia_scale * tp.inv_h2;
+        for (int i = tid; i < np; i += NT) {
+            T e0 = T(0), e1 = T(0), e2 = T(0);
+            if (i < n) {
+                const T mm = ms * __ldg(&tp.mass[i]);
+                T h0 = mm * R[i], h1 = mm * R[np + i], h2 = mm * R[2 * np + i];
+                const int b0 = __ldg(&tp.h_ptr[i]), b1 = __ldg(&tp.h_ptr[i + 1]);
+                for (int p = b0; p < b1; ++p) {
+                    const T lv = __ldg(&tp.h_val[p]);
+                    const int j = __ldg(&tp.h_idx[p]);
+                    h0 += lv * R[j];
+                    h1 += lv * R[np + j];
+                    h2 += lv * R[2 * np + j];
+                }
+                e0 = src[i] - h0;
+                e1 = src[np + i] - h1;
+                e2 = src[2 * np + i] - h2;
+            }
+            tmp[i] = e0;
+            tmp[np + i] = e1;
+            tmp[2 * np + i] = e2;
+        }
+        __syncthreads();
+        src = tmp;
+    }
     for (int q = tid; q < chunks; q += NT) {
         const int c = q / (kpad >> 3), kb = q - c * (kpad >> 3);
         float v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int k = 8 * kb + u;
-            float val = 0.f;
-            if (k < n) {
-                val = (float)src[c * np + k];
-                if (with_residual) {
-                    float hr = ms * (float)__ldg(&tp.mass[k]) * (float)R[c * np + k];
-                    const int b0 = __ldg(&tp.h_ptr[k]), b1 = __ldg(&tp.h_ptr[k + 1]);
-                    for (int p = b0; p < b1; ++p) hr += __ldg(&tp.h_val[p]) * (float)R[c * np + __ldg(&tp.h_idx[p])];
-                    val -= hr;
-                }
-            }
-            v[u] = val;
+            v[u] = k < n ? (float)src[c * np + k] : 0.f;
         }
         const uint4 w = make_uint4(tc::pack_bf16(v[0], v[1]), tc::pack_bf16(v[2], v[3]), tc::pack_bf16(v[4], v[5]),
                                    tc::pack_bf16(v[6], v[7]));
@@ -1273,7 +1296,7 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
                     const int N3 = 3 * np;
                     for (int e = tid; e < N3; e += blockDim.x) S.ut[e] = S.GCv[e];
                     __syncthreads();
-                    tc_post(tp, phase == PH_DIR1 ? S.Dv : S.g, S.GCv, true, bbuf, rank, cs);
+                    tc_post(tp, phase == PH_DIR1 ? S.Dv : S.g, S.GCv, true, bbuf, rank, cs, S.WRv);
                     phase = phase == PH_DIR1 ? PH_DIR2 : PH_FB2;
                     need = true;
                     break;
@@ -1287,7 +1310,7 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
                     S.second_loop();
                     if (!S.descent()) {
                         S.count = 0;
-                        tc_post(tp, S.g, S.GCv, false, bbuf, rank, cs);
+                        tc_post(tp, S.g, S.GCv, false, bbuf, rank, cs, S.WRv);
                         phase = PH_FB1;
                         need = true;
                         break;
@@ -1307,7 +1330,7 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
                 continue;
             }
             S.first_loop();
-            tc_post(tp, S.Dv, S.GCv, false, bbuf, rank, cs);
+            tc_post(tp, S.Dv, S.GCv, false, bbuf, rank, cs, S.WRv);
             phase = PH_DIR1;
             need = true;
             break;
