@@ -199,6 +199,60 @@ int npfem_get_inverse(npfem_handle* h, double* out_host);
    {V0, A0, mean rest edge length, total mass} (4 doubles) to host memory. */
 int npfem_get_rest_info(npfem_handle* h, double* masses_host, double* scalars_host);
 
+/* ---- learned warm start (an addition to the paper's method; the paper has no
+   counterpart).  A per-vertex MLP (9 -> 64 -> 64 -> 3, tanh, BF16 weights, FP32
+   accumulation) proposes the first iterate x^(1) = y + R MLP(features) instead of
+   the first guess y of Algorithm 1; the quasi-Newton iteration then runs to the
+   same residual tolerance, so the result does not depend on the network.  R is the
+   mass-weighted best-fit rotation of the rest shape onto y; the features of vertex
+   i are d_i = R^T (y_i - y_cm) - (X_i - X_cm), its cotangent Laplacian over the
+   one-ring, and R^T F_ext,i h^2 / m_i.  Parameters are packed FP32:
+   W1[64][9] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] mu[9] sigma[9] s_out[3]
+   (5016 values; inputs are normalised as (f - mu) / sigma, outputs scaled by
+   s_out).  All pointers below are device pointers unless named _host. ---- */
+
+/* Number of packed parameters (5016). */
+int npfem_mlp_nparam(void);
+
+/* Training features (FP32, [n_cells * n_verts][9]) of n_cells cells of handle h at
+   their first guess y, from x, v, f (device SoA, FP32); if x_next (the converged
+   x_{n+1}) is given, also the rest-frame targets R^T (x_{n+1} - y) into target
+   ([n_cells * n_verts][3]).  FP32-state handles only.  Errors: INVALID_ARG, CUDA. */
+int npfem_ws_features(npfem_handle* h, int n_cells, const float* x, const float* v, const float* f, const float* x_next,
+                      float* feat, float* target, void* stream);
+
+/* Mean squared error of the normalised output over n samples (rows idx[0..n) of
+   feat/target, or the first n rows if idx is NULL) and its gradient with respect to
+   the 4995 weights and biases (grad: 5016 floats, overwritten; the normalisation
+   entries stay 0; loss: 1 float, overwritten).  The forward pass is the inference
+   network's: BF16-rounded weights, and BF16-rounded operands (normalised inputs,
+   first hidden layer) for the two hidden-layer products; the gradient passes the
+   operand rounding straight through.  Errors: INVALID_ARG, CUDA. */
+int npfem_mlp_loss_grad(const float* params, const float* feat, const float* target, const int32_t* idx, int n,
+                        float* grad, float* loss, void* stream);
+
+/* One Adam step (Kingma & Ba, bias-corrected; step >= 1) on the weights and biases of
+   params with moment buffers m, v (5016 floats each, caller-owned). */
+int npfem_mlp_adam(float* params, float* m, float* v, const float* grad, int step, float lr, float beta1, float beta2,
+                   float eps, void* stream);
+
+/* Network outputs (physical units, rest frame, [n][3]) for n feature rows, with the
+   arithmetic of the solver's warm start (BF16 operands, FP32 accumulation);
+   scratch: 7584 floats (the device layout of the network). */
+int npfem_mlp_predict(const float* params, const float* feat, int n, float* out, float* scratch, void* stream);
+
+/* Installs (mode 1: always use the learned first iterate; mode 2: use it only when
+   it lowers g, at the cost of one more evaluation) or removes (mode 0,
+   params_host = NULL) the warm start of a handle; the weights are rounded to BF16.
+   Blocks.  FP32-state handles only.  Errors: INVALID_ARG, OOM, CUDA. */
+int npfem_set_warmstart(npfem_handle* h, const float* params_host, int mode);
+
+/* First iterate of the step (positions, device SoA FP32) for n_cells cells of h
+   with the handle's current warm start: y, or y + R MLP(features).  Used to check
+   the warm start against a reference.  Errors: INVALID_ARG, CUDA. */
+int npfem_ws_guess(npfem_handle* h, int n_cells, const float* x, const float* v, const float* f, float* x1,
+                   void* stream);
+
 /* Synchronises the handle's device and reports whether a bounded device-side wait
    of a previous step gave up (the tensor-core path waits for its MMAs with an
    iteration limit): returns NPFEM_ERR_TIMEOUT and clears the flag if so, else 0.

@@ -881,3 +881,245 @@ int or_step_batch(const or_model *m, int ncells, int steps, double *x, double *v
     free(th); free(jobs);
     return 0;
 }
+
+/* ======================================================================== */
+/* Learned warm start (an addition to the paper's method, not in the paper): */
+/* a per-vertex MLP proposes x^(1) = y + R MLP(features) before the          */
+/* quasi-Newton iteration; the iteration still runs to the same residual.    */
+/* Plain FP64 reference of the features, the network and its gradient.      */
+/* ======================================================================== */
+#define MLP_IN 9
+#define MLP_H 64
+#define MLP_OUT 3
+/* packed parameters: W1[64][9] b1[64] W2[64][64] b2[64] W3[3][64] b3[3]
+   mu[9] sigma[9] s_out[3]  (the last three are fixed normalisation constants) */
+enum {
+    P_W1 = 0,
+    P_B1 = P_W1 + MLP_H * MLP_IN,
+    P_W2 = P_B1 + MLP_H,
+    P_B2 = P_W2 + MLP_H * MLP_H,
+    P_W3 = P_B2 + MLP_H,
+    P_B3 = P_W3 + MLP_OUT * MLP_H,
+    P_MU = P_B3 + MLP_OUT,
+    P_SIG = P_MU + MLP_IN,
+    P_SOUT = P_SIG + MLP_IN,
+    P_COUNT = P_SOUT + MLP_OUT
+};
+
+int or_mlp_nparam(void) { return P_COUNT; }
+
+/* round a double holding an FP32 value to the nearest BF16 (ties to even), as the
+   network's weights are stored */
+double or_bf16(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x; /* inf / nan */
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double wq(const double *P, int i, int bf16) { return bf16 ? or_bf16(P[i]) : P[i]; }
+
+/* forward pass for one sample; keeps the activations for the backward pass.  With
+   bf16 the network is the one the GPU evaluates on BF16 tensor-core operands: the
+   weights, the normalised inputs (xn) and the first hidden layer (h1q, the operand
+   of the second product) are rounded to BF16; h1 keeps the unrounded tanh for the
+   derivative, so the gradient passes the operand rounding straight through. */
+static void mlp_fwd(const double *P, const double *xraw, int bf16, double *xn, double *h1, double *h1q, double *h2,
+                    double *o)
+{
+    for (int i = 0; i < MLP_IN; ++i) {
+        xn[i] = (xraw[i] - P[P_MU + i]) / P[P_SIG + i];
+        if (bf16) xn[i] = or_bf16(xn[i]);
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+        double a = P[P_B1 + j];
+        for (int i = 0; i < MLP_IN; ++i) a += wq(P, P_W1 + j * MLP_IN + i, bf16) * xn[i];
+        h1[j] = tanh(a);
+        h1q[j] = bf16 ? or_bf16(h1[j]) : h1[j];
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+        double a = P[P_B2 + j];
+        for (int i = 0; i < MLP_H; ++i) a += wq(P, P_W2 + j * MLP_H + i, bf16) * h1q[i];
+        h2[j] = tanh(a);
+    }
+    for (int j = 0; j < MLP_OUT; ++j) {
+        double a = P[P_B3 + j];
+        for (int i = 0; i < MLP_H; ++i) a += wq(P, P_W3 + j * MLP_H + i, bf16) * h2[i];
+        o[j] = a;
+    }
+}
+
+/* network output in physical units (rest frame): o * s_out */
+void or_mlp_predict(const double *P, const double *feat, int n, double *out, int bf16)
+{
+    double xn[MLP_IN], h1[MLP_H], h1q[MLP_H], h2[MLP_H], o[MLP_OUT];
+    for (int s = 0; s < n; ++s) {
+        mlp_fwd(P, feat + MLP_IN * s, bf16, xn, h1, h1q, h2, o);
+        for (int c = 0; c < MLP_OUT; ++c) out[MLP_OUT * s + c] = o[c] * P[P_SOUT + c];
+    }
+}
+
+/* loss = (1/n) sum_s sum_c (o_c - t_c / s_out_c)^2 and its gradient with respect to
+   W1, b1, W2, b2, W3, b3 (zero for the normalisation constants); with bf16 the
+   forward pass is the BF16-operand network of mlp_fwd and the gradient is taken
+   through its rounded weights and operands */
+double or_mlp_loss_grad(const double *P, const double *feat, const double *target, int n, double *grad, int bf16)
+{
+    memset(grad, 0, sizeof(double) * P_COUNT);
+    double loss = 0.0;
+    double xn[MLP_IN], h1[MLP_H], h1q[MLP_H], h2[MLP_H], o[MLP_OUT], d2[MLP_H], d1[MLP_H];
+    for (int s = 0; s < n; ++s) {
+        mlp_fwd(P, feat + MLP_IN * s, bf16, xn, h1, h1q, h2, o);
+        double dout[MLP_OUT];
+        for (int c = 0; c < MLP_OUT; ++c) {
+            double r = o[c] - target[MLP_OUT * s + c] / P[P_SOUT + c];
+            loss += r * r;
+            dout[c] = 2.0 * r / n;
+        }
+        for (int c = 0; c < MLP_OUT; ++c) {
+            grad[P_B3 + c] += dout[c];
+            for (int i = 0; i < MLP_H; ++i) grad[P_W3 + c * MLP_H + i] += dout[c] * h2[i];
+        }
+        for (int i = 0; i < MLP_H; ++i) {
+            double a = 0.0;
+            for (int c = 0; c < MLP_OUT; ++c) a += dout[c] * wq(P, P_W3 + c * MLP_H + i, bf16);
+            d2[i] = a * (1.0 - h2[i] * h2[i]);
+        }
+        for (int j = 0; j < MLP_H; ++j) {
+            grad[P_B2 + j] += d2[j];
+            for (int i = 0; i < MLP_H; ++i) grad[P_W2 + j * MLP_H + i] += d2[j] * h1q[i];
+        }
+        for (int i = 0; i < MLP_H; ++i) {
+            double a = 0.0;
+            for (int j = 0; j < MLP_H; ++j) a += d2[j] * wq(P, P_W2 + j * MLP_H + i, bf16);
+            d1[i] = a * (1.0 - h1[i] * h1[i]);
+        }
+        for (int j = 0; j < MLP_H; ++j) {
+            grad[P_B1 + j] += d1[j];
+            for (int i = 0; i < MLP_IN; ++i) grad[P_W1 + j * MLP_IN + i] += d1[j] * xn[i];
+        }
+    }
+    return loss / n;
+}
+
+/* symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations: S = V diag(w) V^T */
+static void jacobi3(double S[3][3], double w[3], double V[3][3])
+{
+    double A[3][3];
+    memcpy(A, S, sizeof(A));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        if (off < 1e-300) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0) continue;
+                double th = 0.5 * (A[q][q] - A[p][p]) / A[p][q];
+                double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; ++i) w[i] = A[i][i];
+}
+
+/* Best-fit rotation of the rest shape onto y (mass-weighted): the orthogonal polar
+   factor R = A (A^T A)^{-1/2} of A = sum_i m_i (y_i - y_cm)(X_i - X_cm)^T. */
+void or_best_rotation(const or_model *m, const double *y, double *Rout, double *ycm, double *xcm)
+{
+    int n = m->n;
+    double mt = 0.0;
+    for (int r = 0; r < 3; ++r) { ycm[r] = 0.0; xcm[r] = 0.0; }
+    for (int i = 0; i < n; ++i) {
+        mt += m->mass[i];
+        for (int r = 0; r < 3; ++r) { ycm[r] += m->mass[i] * y[3 * i + r]; xcm[r] += m->mass[i] * m->X[3 * i + r]; }
+    }
+    for (int r = 0; r < 3; ++r) { ycm[r] /= mt; xcm[r] /= mt; }
+    double A[3][3] = {{0}};
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) A[a][b] += m->mass[i] * (y[3 * i + a] - ycm[a]) * (m->X[3 * i + b] - xcm[b]);
+    double S[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) S[a][b] = A[0][a] * A[0][b] + A[1][a] * A[1][b] + A[2][a] * A[2][b];
+    double w[3], V[3][3], Sm[3][3];
+    jacobi3(S, w, V);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += V[a][k] * V[b][k] / sqrt(w[k]);
+            Sm[a][b] = s;
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Rout[3 * a + b] = A[a][0] * Sm[0][b] + A[a][1] * Sm[1][b] + A[a][2] * Sm[2][b];
+}
+
+/* Per-vertex raw features at the first guess y (rest frame of the best fit):
+   d_i = R^T (y_i - y_cm) - (X_i - X_cm); lap_i = sum_j c_ij (d_j - d_i);
+   f_i' = R^T F_ext,i h^2 / m_i.  feat: [n][9]. */
+void or_ws_features(const or_model *m, const double *y, const double *f, double *feat, double *Rout)
+{
+    int n = m->n;
+    double ycm[3], xcm[3];
+    or_best_rotation(m, y, Rout, ycm, xcm);
+    const double *R = Rout;
+    double *d = (double *)malloc(sizeof(double) * 3 * n);
+    for (int i = 0; i < n; ++i)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int a = 0; a < 3; ++a) s += R[3 * a + b] * (y[3 * i + a] - ycm[a]);
+            d[3 * i + b] = s - (m->X[3 * i + b] - xcm[b]);
+        }
+    for (int i = 0; i < n; ++i) {
+        double lap[3] = {0, 0, 0};
+        for (int q = m->ring_ptr[i]; q < m->ring_ptr[i + 1]; ++q) {
+            int j = m->ring_idx[q];
+            for (int r = 0; r < 3; ++r) lap[r] += m->ring_c[q] * (d[3 * j + r] - d[3 * i + r]);
+        }
+        double sc = m->h * m->h / m->mass[i];
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int a = 0; a < 3; ++a) s += R[3 * a + b] * f[3 * i + a];
+            feat[9 * i + b] = d[3 * i + b];
+            feat[9 * i + 3 + b] = lap[b];
+            feat[9 * i + 6 + b] = s * sc;
+        }
+    }
+    free(d);
+}
+
+/* Warm-started first guess: x1 = y + R (s_out * MLP(features)). */
+void or_ws_guess(const or_model *m, const double *P, const double *x, const double *v, const double *f, double *x1,
+                 int bf16)
+{
+    int n = m->n;
+    double *y = (double *)malloc(sizeof(double) * 3 * n), *feat = (double *)malloc(sizeof(double) * 9 * n);
+    double *o = (double *)malloc(sizeof(double) * 3 * n), R[9];
+    or_first_guess(m, x, v, f, y);
+    or_ws_features(m, y, f, feat, R);
+    or_mlp_predict(P, feat, n, o, bf16);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) x1[3 * i + a] = y[3 * i + a] + R[3 * a + 0] * o[3 * i] + R[3 * a + 1] * o[3 * i + 1] + R[3 * a + 2] * o[3 * i + 2];
+    free(y); free(feat); free(o);
+}

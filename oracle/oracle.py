@@ -87,6 +87,15 @@ def lib():
         L.or_post_step.argtypes = [P, dp, dp, C.c_double]
         L.or_step.restype = C.c_int
         L.or_step.argtypes = [P, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats)]
+        L.or_mlp_nparam.restype = C.c_int
+        L.or_bf16.restype = C.c_double
+        L.or_bf16.argtypes = [C.c_double]
+        L.or_mlp_predict.argtypes = [dp, dp, C.c_int, dp, C.c_int]
+        L.or_mlp_loss_grad.restype = C.c_double
+        L.or_mlp_loss_grad.argtypes = [dp, dp, dp, C.c_int, dp, C.c_int]
+        L.or_best_rotation.argtypes = [P, dp, dp, dp, dp]
+        L.or_ws_features.argtypes = [P, dp, dp, dp, dp]
+        L.or_ws_guess.argtypes = [P, dp, dp, dp, dp, dp, C.c_int]
         L.or_step_batch.restype = C.c_int
         L.or_step_batch.argtypes = [P, C.c_int, C.c_int, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats), C.c_int]
         _lib = L
@@ -111,6 +120,29 @@ def skalak_f(l, B, D):
 
 def skalak_fp(l, B, D):
     return lib().or_skalak_fp(float(l), float(B), float(D))
+
+
+def mlp_nparam() -> int:
+    return lib().or_mlp_nparam()
+
+
+def bf16(x: float) -> float:
+    return lib().or_bf16(float(x))
+
+
+def mlp_predict(P, feat, bf16_operands=True):
+    feat = np.ascontiguousarray(feat, dtype=np.float64)
+    out = np.zeros((feat.shape[0], 3))
+    lib().or_mlp_predict(np.ascontiguousarray(P, dtype=np.float64), feat, feat.shape[0], out, int(bf16_operands))
+    return out
+
+
+def mlp_loss_grad(P, feat, target, bf16_operands=True):
+    feat = np.ascontiguousarray(feat, dtype=np.float64)
+    g = np.zeros(mlp_nparam())
+    loss = lib().or_mlp_loss_grad(np.ascontiguousarray(P, dtype=np.float64), feat,
+                                  np.ascontiguousarray(target, dtype=np.float64), feat.shape[0], g, int(bf16_operands))
+    return loss, g
 
 
 class Model:
@@ -227,6 +259,21 @@ class Model:
         st = Stats()
         lib().or_step(self._h, x, v, np.ascontiguousarray(f, dtype=np.float64), C.byref(opts or make_opts()), C.byref(st))
         return x, v, st
+
+    def best_rotation(self, y):
+        R = np.zeros(9); yc = np.zeros(3); xc = np.zeros(3)
+        lib().or_best_rotation(self._h, np.ascontiguousarray(y, dtype=np.float64), R, yc, xc)
+        return R.reshape(3, 3), yc, xc
+
+    def ws_features(self, y, f):
+        feat = np.zeros((self.n, 9)); R = np.zeros(9)
+        lib().or_ws_features(self._h, np.ascontiguousarray(y, dtype=np.float64), np.ascontiguousarray(f, dtype=np.float64), feat, R)
+        return feat, R.reshape(3, 3)
+
+    def ws_guess(self, P, x, v, f, bf16_operands=True):
+        x1 = np.zeros((self.n, 3))
+        lib().or_ws_guess(self._h, np.ascontiguousarray(P, dtype=np.float64), *(np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, f)), x1, int(bf16_operands))
+        return x1
 
     def step_batch(self, x, v, f, opts: Opts | None = None, steps: int = 1, threads: int = 1):
         """steps time steps of every cell of [cells, n, 3] arrays (the same force each step)."""

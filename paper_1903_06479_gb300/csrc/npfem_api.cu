@@ -98,6 +98,8 @@ int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv)
     if ((rc = upload(h, ridx, &tp->ring_idx))) return rc;
     if ((rc = upload(h, H.ring_c, &tp->ring_c))) return rc;
     if ((rc = upload(h, H.ring_ct, &tp->ring_ct))) return rc;
+    if ((rc = upload(h, H.rest_c, &tp->rest_c))) return rc;
+    tp->mlp = nullptr;
     if ((rc = upload(h, H.inc_ptr, &tp->inc_ptr))) return rc;
     std::vector<unsigned> incu(H.inc_idx.begin(), H.inc_idx.end());
     if ((rc = upload(h, incu, &tp->inc_idx))) return rc;
@@ -145,7 +147,8 @@ int check_opts(const npfem_opts* o)
 
 template <typename T>
 int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T* x, T* v, const T* f, const T* y,
-              T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream)
+              T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream,
+              const T* u0 = nullptr)
 {
     npfem_handle* h0 = meshes[0];
     LaunchArgs<T> a;
@@ -188,6 +191,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     a.p.armijo_noise = h0->opts.armijo_noise;
     a.p.mode = mode;
     a.p.contraction = CONTRACT_SIMT;
+    a.u0 = u0;
 
     const int threads = h0->threads;
     const int smem = kFixedSmem + smem_max;
@@ -215,11 +219,12 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
 
 // One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
 int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
-                 cudaStream_t stream)
+                 cudaStream_t stream, const float* u0)
 {
     if (cells == 0) return 0;
     LaunchArgs<float> a;
     memset(&a, 0, sizeof(a));
+    a.u0 = u0;
     GroupDesc<float>& g = a.g[0];
     g.topo = h->tf;
     g.cell_begin = 0;
@@ -272,6 +277,41 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     }
     int grid = 0;
     NPFEM_CUDA(launch_cells_tc(a, cluster, h->threads, smem, stream, &grid));
+    return 0;
+}
+
+// Learned first increments of every group with a warm start, into meshes[0]'s
+// buffer at the groups' state offsets (a separate launch: in the cluster kernel a
+// block computing them would hold up its whole cluster).  Null when no group has one.
+int precompute_warm_start(npfem_handle* const* meshes, int n_groups, const int32_t* cells, const float* x,
+                          const float* v, const float* f, cudaStream_t s, const float** u0)
+{
+    *u0 = nullptr;
+    bool any = false;
+    size_t total = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        any = any || (meshes[g]->tf.ws_mode && meshes[g]->tf.mlp && cells[g] > 0);
+        total += (size_t)3 * meshes[g]->n * cells[g];
+    }
+    if (!any) return 0;
+    npfem_handle* h0 = meshes[0];
+    if (total > h0->ws_u_len) {
+        if (h0->ws_u) {
+            NPFEM_CUDA(cudaStreamSynchronize(s));
+            cudaFree(h0->ws_u);
+            h0->ws_u = nullptr;
+            h0->ws_u_len = 0;
+        }
+        NPFEM_CUDA(cudaMalloc(&h0->ws_u, total * sizeof(float)));
+        h0->ws_u_len = total;
+    }
+    size_t off = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        if (meshes[g]->tf.ws_mode && meshes[g]->tf.mlp && cells[g] > 0)
+            NPFEM_CUDA(launch_ws_increments(meshes[g], cells[g], x + off, v + off, f + off, h0->ws_u + off, false, s));
+        off += (size_t)3 * meshes[g]->n * cells[g];
+    }
+    *u0 = h0->ws_u;
     return 0;
 }
 
@@ -436,6 +476,12 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
     DeviceGuard guard(meshes[0]->device);
     std::lock_guard<std::mutex> lk(meshes[0]->mu);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float* u0 = nullptr;
+    if (meshes[0]->precision != NPFEM_PREC_FP64) {
+        if (int rc = precompute_warm_start(meshes, n_groups, cells_per_group, (const float*)x, (const float*)v,
+                                           (const float*)f_ext, s, &u0))
+            return rc;
+    }
     if (meshes[0]->precision == NPFEM_PREC_BF16) {
         bool all_tc = true;
         for (int g = 0; g < n_groups; ++g) all_tc = all_tc && meshes[g]->n <= kTcMaxVerts;
@@ -443,7 +489,8 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
             long long cell0 = 0, state0 = 0;
             for (int g = 0; g < n_groups; ++g) {
                 int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + state0, (float*)v + state0,
-                                      (const float*)f_ext + state0, stats ? stats + cell0 : nullptr, s);
+                                      (const float*)f_ext + state0, stats ? stats + cell0 : nullptr, s,
+                                      u0 ? u0 + state0 : nullptr);
                 if (rc) return rc;
                 cell0 += cells_per_group[g];
                 state0 += 3LL * meshes[g]->n * cells_per_group[g];
@@ -455,7 +502,7 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
         return run_cells<double>(meshes, n_groups, cells_per_group, (double*)x, (double*)v, (const double*)f_ext,
                                  nullptr, nullptr, nullptr, stats, 0, s);
     return run_cells<float>(meshes, n_groups, cells_per_group, (float*)x, (float*)v, (const float*)f_ext, nullptr,
-                            nullptr, nullptr, stats, 0, s);
+                            nullptr, nullptr, stats, 0, s, u0);
 }
 
 int npfem_step_host(npfem_handle* h, int n_cells, void* x_host, void* v_host, const void* f_host, double dt,
@@ -514,6 +561,18 @@ int npfem_eval(npfem_handle* h, int n_cells, const void* x, const void* y, void*
                                  nullptr, 1, s);
     return run_cells<float>(hs, 1, &cells, (float*)x, nullptr, nullptr, (const float*)y, (float*)grad, parts, nullptr,
                             1, s);
+}
+
+int npfem_ws_guess(npfem_handle* h, int n_cells, const float* x, const float* v, const float* f, float* x1, void* stream)
+{
+    if (!h || n_cells < 0 || !x || !v || !f || !x1) return fail(NPFEM_ERR_INVALID_ARG, "npfem_ws_guess: null argument");
+    if (h->precision == NPFEM_PREC_FP64) return fail(NPFEM_ERR_INVALID_ARG, "npfem_ws_guess: FP32 state handles only");
+    DeviceGuard guard(h->device);
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (!h->tf.ws_mode || !h->tf.mlp) return fail(NPFEM_ERR_INVALID_ARG, "npfem_ws_guess: no warm start installed");
+    if (n_cells == 0) return 0;
+    NPFEM_CUDA(launch_ws_increments(h, n_cells, x, v, f, x1, true, static_cast<cudaStream_t>(stream)));
+    return 0;
 }
 
 int npfem_check_device(npfem_handle* h)

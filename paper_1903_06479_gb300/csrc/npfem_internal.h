@@ -51,6 +51,9 @@ struct TopoDev {
     const unsigned short* h_idx;
     const float* h_val;
     int kpad, rb;                // tensor-core path: K padded to 16, row blocks of 128
+    const T* rest_c;             // [3][n] rest positions about the rest centre of mass
+    const float* mlp;            // learned warm start: packed parameters, weights rounded to BF16 (or null)
+    int ws_mode;                 // 0 none, 1 learned first iterate, 2 learned iterate kept only if g is lower
     T C, B, Dsk, kvol;           // material
     T h, inv_h2, inertia_scale;  // time step; inertia_scale = 1 + h alpha_D
     T kappa, lbar, inv_lbar;
@@ -71,7 +74,7 @@ struct GroupDesc {
 struct SolverParams {
     int lbfgs_m, max_iter, max_halvings, fixed_alpha;
     double tol, c1, c2, armijo_noise;
-    int mode;         // 0 = time step, 1 = objective/gradient evaluation only
+    int mode;         // 0 = time step, 1 = objective/gradient evaluation
     int contraction;  // Contraction
     int cluster;      // tensor-core path: blocks per cluster (= row blocks of A^-1)
     int refine;       // tensor-core path: refinement sweeps (0 or 1)
@@ -87,6 +90,7 @@ struct LaunchArgs {
     const T* f;
     const T* y;        // eval mode: inertia target
     T* grad_out;       // eval mode
+    const T* u0;       // precomputed learned first increments x^(1) - x_n ([3][n] per cell) or null
     double* parts;     // eval mode: 8 doubles per cell
     npfem_cell_stats* stats;
     char* scratch;     // per-CTA global slots for vectors that do not fit in smem
@@ -105,6 +109,7 @@ struct HostTopo {
     std::vector<double> ring_c;               // c_ij for entry (i, j)
     std::vector<double> ring_ct;              // c_ji for entry (i, j): weight of i in the ring of j
     std::vector<int> inc_ptr, inc_idx;        // vertex -> incident (triangle << 2 | corner)
+    std::vector<double> rest_c;               // [3][n] rest positions about the rest centre of mass
     std::vector<int> L_ptr, L_idx;            // CSR of L (full symmetric)
     std::vector<double> L_val;
     double V0 = 0, A0 = 0, lbar = 0, mtotal = 0;
@@ -133,6 +138,10 @@ cudaError_t set_cell_kernel_smem(int bytes);
 // mesh group; sets *grid_out.
 cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, int smem, cudaStream_t s,
                             int* grid_out);
+// Learned first increments u = x^(1) - x_n ([3][n] per cell, or positions x_n + u
+// when positions is set) of n_cells cells of handle h (npfem_learn.cu).
+cudaError_t launch_ws_increments(const npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
+                                 float* out, bool positions, cudaStream_t s);
 // Largest mesh the tensor-core path takes: A block (kpad / 2 columns) plus a
 // 32-column accumulator within 512 TMEM columns, and at most 8 blocks per cluster.
 constexpr int kTcMaxVerts = 960;
@@ -148,10 +157,13 @@ inline void place_vectors(GroupDesc<T>* g, int n_pad, int nt, int m, int smem_bu
                           int base_off = 0)
 {
     const int vb = 3 * n_pad * (int)sizeof(T);
-    // TRI also serves as the contraction's scratch: (max(32 warps, row tiles) x 384 floats)
+    // TRI also serves as the contraction's scratch (max(32 warps, row tiles) x 384
+    // floats) and holds the warm start's normalised features ([n rounded to 16][16] floats)
     const int tri_bytes = 9 * nt * (int)sizeof(T);
     const int ctr_bytes = (((n_pad + 127) / 128) > 32 ? ((n_pad + 127) / 128) : 32) * 384 * 4;
-    const int tb = ((tri_bytes > ctr_bytes ? tri_bytes : ctr_bytes) + 15) & ~15;
+    const int ws_bytes = ((n_pad + 15) & ~15) * 16 * 4;
+    int tb = tri_bytes > ctr_bytes ? tri_bytes : ctr_bytes;
+    tb = ((tb > ws_bytes ? tb : ws_bytes) + 15) & ~15;
     int order[kMaxVecs], nv = 0;
     const int base[kNumBaseVecs] = {V_XN, V_U, V_UT, V_TRI, V_WR, V_G, V_GT, V_GC, V_UY, V_D};
     for (int q = 0; q < kNumBaseVecs; ++q) order[nv++] = base[q];
@@ -195,9 +207,12 @@ struct npfem_handle {
     unsigned int* work = nullptr;
     char* scratch = nullptr;
     size_t scratch_bytes = 0;
+    float* ws_u = nullptr;  // learned first increments of the cluster kernel's cells
+    size_t ws_u_len = 0;
     int sm_count = 0, smem_optin = 0;
     int threads = 512;
     // buffers of npfem_step_host
+    float* mlp = nullptr;       // learned warm start parameters on the device (weights BF16-rounded)
     void* hx = nullptr;
     void* hv = nullptr;
     void* hf = nullptr;
@@ -225,6 +240,9 @@ struct npfem_handle {
         if (scratch) cudaFree(scratch);
         scratch = nullptr;
         scratch_bytes = 0;
+        if (ws_u) cudaFree(ws_u);
+        ws_u = nullptr;
+        ws_u_len = 0;
         if (hx) cudaFree(hx);
         if (hv) cudaFree(hv);
         if (hf) cudaFree(hf);

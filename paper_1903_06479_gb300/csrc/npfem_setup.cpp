@@ -222,6 +222,23 @@ int build_host_topo(const npfem_mesh* mesh, const npfem_material* mat, int equal
     o->mtotal = mat->density * V0;
     o->mass.assign(n, 0.0);
     for (int i = 0; i < n; ++i) o->mass[i] = equal_mass ? o->mtotal / n : o->mtotal * bary[i] / A0;
+    // rest positions about the rest centre of mass (frame of the learned warm start)
+    {
+        V3 cm{0, 0, 0};
+        double mt = 0.0;
+        for (int i = 0; i < n; ++i) {
+            cm = add(cm, scale(X(i), o->mass[i]));
+            mt += o->mass[i];
+        }
+        cm = scale(cm, 1.0 / mt);
+        o->rest_c.assign(3 * (size_t)n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            const V3 r = sub(X(i), cm);
+            o->rest_c[i] = r.x;
+            o->rest_c[n + i] = r.y;
+            o->rest_c[2 * n + i] = r.z;
+        }
+    }
 
     // --- L = sum_i w_i G_i^T G_i (sparse)
     RowAccum L(n);

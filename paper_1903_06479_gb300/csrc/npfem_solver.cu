@@ -21,222 +21,12 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "npfem_device.cuh"
 #include "npfem_internal.h"
+#include "npfem_ws.cuh"
 
 namespace npfem {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-template <typename T>
-struct Unit;
-template <>
-struct Unit<float> {
-    static constexpr double u = 5.9604644775390625e-08;
-    static constexpr float sl2_rel = 2.0e-7f;
-    static constexpr float tiny = 1.0e-37f;
-};
-template <>
-struct Unit<double> {
-    static constexpr double u = 1.1102230246251565e-16;
-    static constexpr double sl2_rel = 4.0e-16;
-    static constexpr double tiny = 1.0e-300;
-};
-
-// Compensated sum (hi + lo) built from error-free two-sums.
-template <typename T>
-struct Acc {
-    T hi, lo;
-    __device__ __forceinline__ Acc() : hi(T(0)), lo(T(0)) {}
-    __device__ __forceinline__ void add(T x)
-    {
-        const T s = hi + x;
-        const T bb = s - hi;
-        lo += (hi - (s - bb)) + (x - bb);
-        hi = s;
-    }
-    __device__ __forceinline__ void merge(T h2, T l2)
-    {
-        add(h2);
-        lo += l2;
-    }
-};
-
-// Per-cell scalars shared by the block (after the 8 KB of reduction partials).
-struct CellShared {
-    double out[16];          // results of the last block_reduce
-    double V, Vn, E, Ein, Earea, Esk, Ebend, Evol, res, noise;
-    double rho[kMaxHistory];
-    double alpha[kMaxHistory];
-    double post[12];         // centre of mass, its velocity, angular velocity
-    double volc;
-    long long item;          // work item handed to the block
-    unsigned long long mbar; // tensor-core path: MMA completion barrier
-    unsigned need[16];       // tensor-core path: request flags of the cluster's blocks
-    unsigned taddr;          // tensor-core path: tensor-memory base address
-    int bad;
-    int accept;
-    int push;
-};
-static_assert(sizeof(CellShared) <= kFixedSmem - 8192, "CellShared does not fit");
-
-__device__ __forceinline__ CellShared* cell_shared(unsigned char* smem)
-{
-    return reinterpret_cast<CellShared*>(smem + 8192);
-}
-
-// Sums K compensated accumulators over the block.  Thread 0 writes the totals to
-// sh->out[] and then runs epi(sh) before the closing barrier, so every thread sees
-// the totals and whatever the epilogue derived from them.
-struct NoEpi {
-    __device__ __forceinline__ void operator()(CellShared*) const {}
-};
-
-template <typename T, int K, typename Epi = NoEpi>
-__device__ __forceinline__ void block_reduce(Acc<T> (&a)[K], unsigned char* smem, Epi epi = Epi())
-{
-    T* red = reinterpret_cast<T*>(smem);  // [32 warps][K][2]
-    CellShared* sh = cell_shared(smem);
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const T h2 = __shfl_xor_sync(kFull, a[k].hi, o);
-            const T l2 = __shfl_xor_sync(kFull, a[k].lo, o);
-            a[k].merge(h2, l2);
-        }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            red[(w * K + k) * 2] = a[k].hi;
-            red[(w * K + k) * 2 + 1] = a[k].lo;
-        }
-    }
-    __syncthreads();
-    if (w == 0) {
-        Acc<T> b[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-            if (lane < nw) {
-                b[k].hi = red[(lane * K + k) * 2];
-                b[k].lo = red[(lane * K + k) * 2 + 1];
-            }
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const T h2 = __shfl_xor_sync(kFull, b[k].hi, o);
-                const T l2 = __shfl_xor_sync(kFull, b[k].lo, o);
-                b[k].merge(h2, l2);
-            }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) sh->out[k] = (double)b[k].hi + (double)b[k].lo;
-            epi(sh);
-        }
-    }
-    __syncthreads();
-}
-
-// Like block_reduce, for KC compensated and KP plain sums (out[0..KC) compensated,
-// out[KC..KC+KP) plain).
-template <typename T, int KC, int KP, typename Epi = NoEpi>
-__device__ __forceinline__ void block_reduce_cp(Acc<T> (&a)[KC], T (&p)[KP], unsigned char* smem, Epi epi = Epi())
-{
-    constexpr int W = 2 * KC + KP;
-    T* red = reinterpret_cast<T*>(smem);  // [32 warps][W]
-    CellShared* sh = cell_shared(smem);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            const T h2 = __shfl_xor_sync(kFull, a[k].hi, o);
-            const T l2 = __shfl_xor_sync(kFull, a[k].lo, o);
-            a[k].merge(h2, l2);
-        }
-#pragma unroll
-        for (int k = 0; k < KP; ++k) p[k] += __shfl_xor_sync(kFull, p[k], o);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            red[w * W + 2 * k] = a[k].hi;
-            red[w * W + 2 * k + 1] = a[k].lo;
-        }
-#pragma unroll
-        for (int k = 0; k < KP; ++k) red[w * W + 2 * KC + k] = p[k];
-    }
-    __syncthreads();
-    if (w == 0) {
-        Acc<T> b[KC];
-        T q[KP];
-#pragma unroll
-        for (int k = 0; k < KP; ++k) q[k] = T(0);
-        if (lane < nw) {
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                b[k].hi = red[lane * W + 2 * k];
-                b[k].lo = red[lane * W + 2 * k + 1];
-            }
-#pragma unroll
-            for (int k = 0; k < KP; ++k) q[k] = red[lane * W + 2 * KC + k];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                const T h2 = __shfl_xor_sync(kFull, b[k].hi, o);
-                const T l2 = __shfl_xor_sync(kFull, b[k].lo, o);
-                b[k].merge(h2, l2);
-            }
-#pragma unroll
-            for (int k = 0; k < KP; ++k) q[k] += __shfl_xor_sync(kFull, q[k], o);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < KC; ++k) sh->out[k] = (double)b[k].hi + (double)b[k].lo;
-#pragma unroll
-            for (int k = 0; k < KP; ++k) sh->out[KC + k] = (double)q[k];
-            epi(sh);
-        }
-    }
-    __syncthreads();
-}
-
-// Plain (uncompensated) block sum of K values, for dot products of the direction.
-template <typename T, int K, typename Epi = NoEpi>
-__device__ __forceinline__ void block_sum(T (&p)[K], unsigned char* smem, Epi epi = Epi())
-{
-    T* red = reinterpret_cast<T*>(smem);
-    CellShared* sh = cell_shared(smem);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < K; ++k) p[k] += __shfl_xor_sync(kFull, p[k], o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) red[w * K + k] = p[k];
-    }
-    __syncthreads();
-    if (w == 0) {
-        T q[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) q[k] = lane < nw ? red[lane * K + k] : T(0);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int k = 0; k < K; ++k) q[k] += __shfl_xor_sync(kFull, q[k], o);
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) sh->out[k] = (double)q[k];
-            epi(sh);
-        }
-    }
-    __syncthreads();
-}
 
 // SL(2) projection of the principal stretches (Sec. 2.1.2, area preservation):
 // Sigma* = diag(a, 1/a) closest to diag(s1, s2), s1 >= s2.  With a = 1 + t,
@@ -266,13 +56,6 @@ __device__ __forceinline__ T sl2_t(T e1, T e2)
         if (fabs(step) <= Unit<T>::sl2_rel * (fabs(t) + fabs(e1) + fabs(e2)) + Unit<T>::tiny || hi - lo <= T(0)) break;
     }
     return t;
-}
-
-template <typename T>
-__device__ __forceinline__ T* vec_ptr(const GroupDesc<T>& gd, unsigned char* smem, char* slot, int v)
-{
-    const int l = gd.loc[v];
-    return l >= 0 ? reinterpret_cast<T*>(smem + kFixedSmem + l) : reinterpret_cast<T*>(slot + (-(long long)l - 1));
 }
 
 // Volume of the cell at x_n in local coordinates: V = sum_t X_i . (E1 x E2) / 6.
@@ -514,10 +297,11 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
         const T inv = T(1) / (T)s->out[5];
         s->Evol = 0.5 * kvol * Cv * Cv * (double)inv;
         s->volc = kvol * Cv * (double)inv;
+        s->volcf = (float)s->volc;
         s->noise = s->out[6];
         s->bad = s->out[7] != 0.0;
     });
-    const T volc = (T)sh->volc;
+    const T volc = bcast<T>(sh->volc, sh->volcf);
 
     // ---- pass 3: bending gather, volume and inertia (M~ = (1 + h alpha_D) M), residual
     const T ms = tp.inertia_scale * tp.inv_h2, h2 = tp.h * tp.h;
@@ -737,9 +521,85 @@ struct CellSolver {
             u[e] = eval_mode ? T(0) : uy;
         }
         __syncthreads();
-        evaluate<T, true>(T_, XN, u, UYv, g, GCv, TRIv, WRv, 0.0, smem);
-        Vn = sh->Vn;
+        // learned warm start: u = u_y + R MLP(features at y)
+        const int ws = (!eval_mode && T_.mlp) ? T_.ws_mode : 0;
+        if (ws && a->u0) {
+            const T* U0 = a->u0 + so;
+            for (int e = tid; e < N3; e += NT) {
+                const int c = e / np, i = e - c * np;
+                u[e] = i < n ? U0[c * n + i] : T(0);
+            }
+            __syncthreads();
+        } else if (ws) {
+            for (int e = tid; e < N3; e += NT) ut[e] = XN[e] + UYv[e];
+            __syncthreads();
+            ws_frame(T_, ut, WRv, smem);
+            T R[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) R[q] = sh->postf[q];
+            const T* F = a->f + so;
+            const float* P = T_.mlp;
+            // normalised features of every vertex (one thread each) into the idle
+            // triangle buffer, rows of 16 floats (9 used), zero rows up to a multiple of 16
+            float* Xs = reinterpret_cast<float*>(TRIv);
+            const int n16 = (n + 15) & ~15;
+            for (int i = tid; i < n16; i += NT) {
+                float ft[kMlpIn];
+                if (i < n) ws_vertex_features(T_, WRv, F, i, R, ft);
+                float4* row = reinterpret_cast<float4*>(Xs + 16 * i);
+                float xv[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) xv[k] = (k < kMlpIn && i < n) ? (ft[k] - P[kPMu + k]) / P[kPSig + k] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) row[q] = make_float4(xv[4 * q], xv[4 * q + 1], xv[4 * q + 2], xv[4 * q + 3]);
+            }
+            __syncthreads();
+            // the network on 16-vertex tiles, one warp per tile
+            const int lane = tid & 31;
+            for (int tile = tid >> 5; tile * 16 < n; tile += NT >> 5) {
+                float olo[3], ohi[3];
+                mlp_warp16(P, Xs + 256 * tile, olo, ohi);
+                if ((lane & 3) == 0) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int i = tile * 16 + (lane >> 2) + 8 * r;
+                        if (i >= n) continue;
+                        const float* o = r ? ohi : olo;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            u[c * np + i] = UYv[c * np + i] + (R[3 * c] * (T)o[0] + R[3 * c + 1] * (T)o[1] + R[3 * c + 2] * (T)o[2]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
         evals = 1;
+        if (ws == 2) {
+            // keep the learned guess only if it lowers g: evaluate at y (trial buffers) first
+            for (int e = tid; e < N3; e += NT) ut[e] = UYv[e];
+            __syncthreads();
+            evaluate<T, true>(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, 0.0, smem);
+            Vn = sh->Vn;
+            const double Ey = sh->E, ny = sh->noise, ry = sh->res, Vy = sh->V;
+            const bool by = sh->bad;
+            evaluate<T, false>(T_, XN, u, UYv, g, GCv, TRIv, WRv, Vn, smem);
+            evals = 2;
+            if (!(sh->E <= Ey) && !by) {
+                T* t1 = u; u = ut; ut = t1;
+                T* t2 = g; g = gt; gt = t2;
+                if (tid == 0) {
+                    sh->E = Ey;
+                    sh->noise = ny;
+                    sh->res = ry;
+                    sh->V = Vy;
+                    sh->bad = 0;
+                }
+                __syncthreads();
+            }
+        } else {
+            evaluate<T, true>(T_, XN, u, UYv, g, GCv, TRIv, WRv, 0.0, smem);
+            Vn = sh->Vn;
+        }
         iters = 0;
         status = NPFEM_CELL_OK;
         head = 0;
@@ -839,9 +699,9 @@ struct CellSolver {
         const int N3 = 3 * T_.n_pad, tid = threadIdx.x, NT = blockDim.x;
         const double c1 = a->p.c1, c2 = a->p.c2, anoise = a->p.armijo_noise;
         double alpha = 1.0;
+        T al = T(1);  // alpha in the working type (powers of two: exact)
         bool accepted = false;
         for (int hv = 0; hv <= a->p.max_halvings; ++hv) {
-            const T al = (T)alpha;
             for (int e = tid; e < N3; e += NT) ut[e] = u[e] + al * Dv[e];
             __syncthreads();
             evaluate(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, Vn, smem);
@@ -856,6 +716,7 @@ struct CellSolver {
                 break;
             }
             alpha *= 0.5;
+            al *= T(0.5);
         }
         if (!accepted) {
             status = NPFEM_CELL_LINESEARCH_FAIL;
@@ -940,7 +801,10 @@ struct CellSolver {
         block_reduce<T, 16>(ps, smem, [=](CellShared* s) {
             double* o = s->out;
             double* P = s->post;
-            for (int q = 0; q < 9; ++q) P[q] = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                P[q] = 0.0;
+                s->postf[q] = 0.f;
+            }
             if (nf) return;
             const double Mt = o[0];
             double xc[3], vc[3];
@@ -968,10 +832,15 @@ struct CellSolver {
             P[6] = (c00 * L0 + c01 * L1 + c02 * L2) / det;
             P[7] = (c01 * L0 + c11 * L1 + c12 * L2) / det;
             P[8] = (c02 * L0 + c12 * L1 + c22 * L2) / det;
+            for (int q = 0; q < 9; ++q) s->postf[q] = (float)P[q];
         });
-        const T xc[3] = {(T)sh->post[0], (T)sh->post[1], (T)sh->post[2]};
-        const T vc[3] = {(T)sh->post[3], (T)sh->post[4], (T)sh->post[5]};
-        const T w[3] = {(T)sh->post[6], (T)sh->post[7], (T)sh->post[8]};
+        T xc[3], vc[3], w[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xc[c] = bcast<T>(sh->post[c], sh->postf[c]);
+            vc[c] = bcast<T>(sh->post[3 + c], sh->postf[3 + c]);
+            w[c] = bcast<T>(sh->post[6 + c], sh->postf[6 + c]);
+        }
         const T kap = T_.kappa;
         T* x = a->x + so;
         T* v = a->v + so;

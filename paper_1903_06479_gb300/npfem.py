@@ -48,7 +48,8 @@ CELL_STATS_DTYPE = np.dtype([("iterations", "<i4"), ("evaluations", "<i4"), ("st
 _lib = None
 EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", "npfem_step_host", "npfem_eval",
            "npfem_get_inverse", "npfem_get_rest_info", "npfem_last_error", "npfem_step_static",
-           "npfem_check_device")
+           "npfem_check_device", "npfem_mlp_nparam", "npfem_ws_features", "npfem_mlp_loss_grad", "npfem_mlp_adam",
+           "npfem_mlp_predict", "npfem_set_warmstart", "npfem_ws_guess")
 
 
 def lib_path() -> str:
@@ -73,6 +74,13 @@ def lib():
         L.npfem_get_inverse.argtypes = [vp, vp]
         L.npfem_get_rest_info.argtypes = [vp, vp, vp]
         L.npfem_check_device.argtypes = [vp]
+        L.npfem_mlp_nparam.argtypes = []
+        L.npfem_ws_features.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.npfem_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
+        L.npfem_mlp_adam.argtypes = [vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float, C.c_float, vp]
+        L.npfem_mlp_predict.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.npfem_set_warmstart.argtypes = [vp, vp, i32]
+        L.npfem_ws_guess.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.npfem_last_error.restype = C.c_char_p
         L.npfem_last_error.argtypes = []
         for name in EXPORTS:
@@ -150,6 +158,22 @@ class Handle:
         except Exception:
             pass
 
+    def set_warmstart(self, params: np.ndarray | None, mode: int = 1):
+        """Installs a trained warm-start network (5016 FP32 parameters) or removes it."""
+        if params is None:
+            _check(lib().npfem_set_warmstart(self._h, None, 0))
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            assert p.size == mlp_nparam()
+            _check(lib().npfem_set_warmstart(self._h, p.ctypes.data, int(mode)))
+
+    def ws_features(self, n_cells, x, v, f, feat, x_next=None, target=None, stream=None):
+        _check(lib().npfem_ws_features(self._h, n_cells, _addr(x), _addr(v), _addr(f), _addr(x_next), _addr(feat),
+                                       _addr(target), _addr(stream)))
+
+    def ws_guess(self, n_cells, x, v, f, x1, stream=None):
+        _check(lib().npfem_ws_guess(self._h, n_cells, _addr(x), _addr(v), _addr(f), _addr(x1), _addr(stream)))
+
     def check_device(self):
         """Raises NpfemError(-5) if a bounded device wait of a previous step gave up."""
         _check(lib().npfem_check_device(self._h))
@@ -191,3 +215,22 @@ def step_static(handles, cells_per_group, x, v, f, dt: float, stream=None, stats
     cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
     _check(lib().npfem_step_static(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), _addr(stream),
                                    _addr(stats)))
+
+
+def mlp_nparam() -> int:
+    return lib().npfem_mlp_nparam()
+
+
+def mlp_loss_grad(params, feat, target, idx, n, grad, loss, stream=None):
+    """Mean loss and gradient of the warm-start network over n samples (device pointers)."""
+    _check(lib().npfem_mlp_loss_grad(_addr(params), _addr(feat), _addr(target), _addr(idx), int(n), _addr(grad),
+                                     _addr(loss), _addr(stream)))
+
+
+def mlp_adam(params, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().npfem_mlp_adam(_addr(params), _addr(m), _addr(v), _addr(grad), int(step), float(lr), float(beta1),
+                                float(beta2), float(eps), _addr(stream)))
+
+
+def mlp_predict(params, feat, n, out, scratch, stream=None):
+    _check(lib().npfem_mlp_predict(_addr(params), _addr(feat), int(n), _addr(out), _addr(scratch), _addr(stream)))

@@ -27,8 +27,9 @@ def oracle_steps(model, x, v, f, steps=1, threads=8, **opts):
     return model.step_batch(x, v, f, O.make_opts(**opts), steps=steps, threads=threads)
 
 
-def gpu_step_device(handle, x, v, f, steps=1, dtype="float32", stats=True):
-    """Run npfem_step on torch device tensors built from [cells, n, 3] arrays."""
+def gpu_step_device(handle, x, v, f, steps=1, dtype="float32", stats=True, static=False):
+    """Run npfem_step (npfem_step_static with static) on torch device tensors built
+    from [cells, n, 3] arrays."""
     import torch
     from paper_1903_06479_gb300 import npfem
     td = torch.float64 if dtype == "float64" else torch.float32
@@ -37,8 +38,9 @@ def gpu_step_device(handle, x, v, f, steps=1, dtype="float32", stats=True):
     fs = torch.tensor(W.to_soa(f), dtype=td, device="cuda")
     cells = x.shape[0]
     st = torch.zeros((cells, 32), dtype=torch.uint8, device="cuda") if stats else None
+    fn = npfem.step_static if static else npfem.step
     for _ in range(steps):
-        npfem.step([handle], [cells], xs, vs, fs, handle.dt, stats=st)
+        fn([handle], [cells], xs, vs, fs, handle.dt, stats=st)
     torch.cuda.synchronize()
     out_st = None
     if stats:
