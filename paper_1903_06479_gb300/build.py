@@ -17,6 +17,10 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libnpfem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The solver's FP32 divisions and square roots feed an iteration that stops at a
+# relative residual of ~1e-6; the approximate forms (a few ulp) cut the evaluation's
+# instruction count by about a fifth.  FP64 arithmetic is unaffected by these flags.
+EXTRA = {"npfem_solver.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _nvcc() -> str:
@@ -34,7 +38,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    deps = (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)])
     return any(os.path.getmtime(p) > t for p in deps)
 
 
@@ -47,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *common, *ARCH, "-c", src, "-o", obj]
+        cmd = [nvcc, *common, *ARCH, *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if ptxas_info and src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -103,6 +103,78 @@ int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv)
     if ((rc = upload(h, H.inc_ptr, &tp->inc_ptr))) return rc;
     std::vector<unsigned> incu(H.inc_idx.begin(), H.inc_idx.end());
     if ((rc = upload(h, incu, &tp->inc_idx))) return rc;
+    // Fixed-width tables: each vertex's one-ring in cyclic order r_0 .. r_{v-1} (v <= 8)
+    // so that triangle (i, r_q, r_{q+1 mod v}) is incident triangle q of vertex i, in
+    // the mesh's orientation.  Needs every one-ring to be one cycle of at most 8.
+    std::vector<std::vector<int>> cyc(H.n);
+    bool ok8 = true;
+    {
+        std::vector<std::vector<std::pair<int, int>>> nxt(H.n);  // (j, k) for triangles (i, j, k)
+        for (int t = 0; t < H.nt; ++t)
+            for (int a = 0; a < 3; ++a)
+                nxt[H.tri[3 * t + a]].push_back({H.tri[3 * t + (a + 1) % 3], H.tri[3 * t + (a + 2) % 3]});
+        for (int i = 0; i < H.n && ok8; ++i) {
+            const int v = (int)nxt[i].size();
+            if (v > 8 || v != H.ring_ptr[i + 1] - H.ring_ptr[i]) {
+                ok8 = false;
+                break;
+            }
+            int j = nxt[i][0].first;
+            for (int q = 0; q < v; ++q) {
+                cyc[i].push_back(j);
+                int k = -1;
+                for (const auto& e : nxt[i])
+                    if (e.first == j) k = e.second;
+                if (k < 0) {
+                    ok8 = false;
+                    break;
+                }
+                j = k;
+            }
+            if (ok8 && j != nxt[i][0].first) ok8 = false;
+            if (ok8) {
+                std::vector<int> sc(cyc[i]);
+                std::sort(sc.begin(), sc.end());
+                ok8 = std::adjacent_find(sc.begin(), sc.end()) == sc.end();
+            }
+        }
+    }
+    tp->k8 = ok8 ? 1 : 0;
+    tp->ring8_idx = nullptr;
+    tp->ring8_c = tp->ring8_ct = nullptr;
+    if (tp->k8) {
+        std::vector<unsigned short> r8(8 * (size_t)H.n);
+        std::vector<double> c8(8 * (size_t)H.n, 0.0), ct8(8 * (size_t)H.n, 0.0);
+        for (int i = 0; i < H.n; ++i) {
+            for (int q = 0; q < 8; ++q) r8[8 * i + q] = (unsigned short)i;
+            for (int q = 0; q < (int)cyc[i].size(); ++q) {
+                const int j = cyc[i][q];
+                r8[8 * i + q] = (unsigned short)j;
+                for (int p = H.ring_ptr[i]; p < H.ring_ptr[i + 1]; ++p)
+                    if (H.ring_idx[p] == j) {
+                        c8[8 * i + q] = H.ring_c[p];
+                        ct8[8 * i + q] = H.ring_ct[p];
+                    }
+            }
+        }
+        // slot of each triangle corner in its vertex's cyclic ring, packed 3 bits per
+        // corner into the fourth component of the triangle's index record
+        for (int t = 0; t < H.nt; ++t) {
+            unsigned packed = 0;
+            for (int a = 0; a < 3; ++a) {
+                const int i = H.tri[3 * t + a], j = H.tri[3 * t + (a + 1) % 3];
+                int slot = 0;
+                while (cyc[i][slot] != j) ++slot;
+                packed |= (unsigned)slot << (3 * a);
+            }
+            tri4[4 * t + 3] = (unsigned short)packed;
+        }
+        NPFEM_CUDA(cudaMemcpy(const_cast<unsigned short*>(dtri), tri4.data(), tri4.size() * sizeof(unsigned short),
+                              cudaMemcpyHostToDevice));
+        if ((rc = upload(h, r8, &tp->ring8_idx))) return rc;
+        if ((rc = upload(h, c8, &tp->ring8_c))) return rc;
+        if ((rc = upload(h, ct8, &tp->ring8_ct))) return rc;
+    }
     tp->n = H.n;
     tp->nt = H.nt;
     tp->n_pad = h->n_pad;
@@ -123,6 +195,8 @@ int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv)
     tp->lbar = (T)H.lbar;
     tp->inv_lbar = (T)(1.0 / H.lbar);
     tp->V0 = H.V0;
+    tp->V0hi = (T)H.V0;
+    tp->V0lo = (T)(H.V0 - (double)tp->V0hi);
     return 0;
 }
 
@@ -181,14 +255,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     a.parts = parts;
     a.stats = stats;
     a.work = h0->work;
-    a.p.lbfgs_m = h0->opts.lbfgs_m;
-    a.p.max_iter = h0->opts.max_iter;
-    a.p.max_halvings = h0->opts.max_halvings;
-    a.p.fixed_alpha = h0->opts.fixed_alpha;
-    a.p.tol = h0->opts.tol;
-    a.p.c1 = h0->opts.c1;
-    a.p.c2 = h0->opts.c2;
-    a.p.armijo_noise = h0->opts.armijo_noise;
+    set_solver_params(&a.p, h0->opts);
     a.p.mode = mode;
     a.p.contraction = CONTRACT_SIMT;
     a.u0 = u0;
@@ -235,7 +302,8 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     const int bbytes = (ncol * h->tf.kpad * 2 + 127) & ~127;
     const int budget = h->smem_optin - kFixedSmem - 1024 - bbytes;
     long long slot = 0;
-    place_vectors(&g, h->n_pad, h->nt, h->opts.lbfgs_m, budget, &slot, bbytes);
+    place_vectors(&g, h->n_pad, h->nt, h->opts.lbfgs_m, budget, &slot, bbytes, true);
+    if (g.loc[V_GC] < 0) return fail(NPFEM_ERR_INVALID_ARG, "mesh too large for the tensor-core path's shared memory");
     a.n_groups = 1;
     a.total_cells = cells;
     a.x = x;
@@ -243,14 +311,7 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     a.f = f;
     a.stats = stats;
     a.work = h->work;
-    a.p.lbfgs_m = h->opts.lbfgs_m;
-    a.p.max_iter = h->opts.max_iter;
-    a.p.max_halvings = h->opts.max_halvings;
-    a.p.fixed_alpha = h->opts.fixed_alpha;
-    a.p.tol = h->opts.tol;
-    a.p.c1 = h->opts.c1;
-    a.p.c2 = h->opts.c2;
-    a.p.armijo_noise = h->opts.armijo_noise;
+    set_solver_params(&a.p, h->opts);
     a.p.mode = 0;
     a.p.contraction = CONTRACT_TC_BF16;
     a.p.cluster = cluster;

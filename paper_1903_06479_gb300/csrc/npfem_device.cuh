@@ -45,16 +45,73 @@ struct Acc {
     }
 };
 
-// Per-cell scalars shared by the block (after the 8 KB of reduction partials).
+// A value carried as the unevaluated sum hi + lo of two T (float-float on the FP32
+// path): energies and volumes whose differences the solver takes.
+template <typename T>
+struct Pair {
+    T hi, lo;
+};
+
+template <typename T>
+__device__ __forceinline__ Pair<T> pair_add(Pair<T> a, Pair<T> b)
+{
+    const T s = a.hi + b.hi;
+    const T bb = s - a.hi;
+    const T e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+    const T h = s + e;
+    return {h, e - (h - s)};
+}
+
+template <typename T>
+__device__ __forceinline__ Pair<T> pair_add(Pair<T> a, T b)
+{
+    return pair_add(a, Pair<T>{b, T(0)});
+}
+
+// (hi + lo) / 6 keeping the pair's precision: the remainder of hi / 6 is exact.
+template <typename T>
+__device__ __forceinline__ Pair<T> pair_div6(T hi, T lo)
+{
+    const T q = hi / T(6);
+    return {q, (fma(-q, T(6), hi) + lo) / T(6)};
+}
+
+// a - b, accurate when a and b are close (the high parts subtract exactly).
+template <typename T>
+__device__ __forceinline__ T pair_diff(Pair<T> a, Pair<T> b)
+{
+    return (a.hi - b.hi) + (a.lo - b.lo);
+}
+
+template <typename T>
+__device__ __forceinline__ double pair_f64(Pair<T> a)
+{
+    return (double)a.hi + (double)a.lo;
+}
+
+// Per-cell scalars shared by the block (after the 8 KB of reduction partials), in the
+// solver's type: the FP32 path does no FP64 arithmetic (an FP64 operation costs tens
+// of FP32 ones on this part, a division or square root hundreds).
+template <typename T>
 struct CellShared {
-    double out[16];          // results of the last block_reduce
-    double V, Vn, E, Ein, Earea, Esk, Ebend, Evol, res, noise;
-    double rho[kMaxHistory];
-    double alpha[kMaxHistory];
-    double post[12];         // centre of mass, its velocity, angular velocity
-    float postf[12];         // FP32 copies of post[] and of the warm start's frame (R, y_cm)
-    double volc;
-    float volcf;
+    T out[24];               // results of the last block reduction (high parts of compensated sums)
+    T outlo[16];             // low parts of the compensated sums
+    Pair<T> E, Ein, Earea, Esk, Ebend, V, Vn;
+    T Evol, res, noise, volc;
+    // L-BFGS history, by slot: rho_i = 1 / s_i^T y_i, the two-loop coefficients, the
+    // inner products SY[i][j] = s_i^T y_j of the stored pairs, s_i^T g at the current
+    // iterate, y_i^T r (r = H0 q of the last direction) and alpha_i - beta_i
+    T rho[kMaxHistory];
+    T alpha[kMaxHistory];
+    T SY[kMaxHistory][kMaxHistory];
+    T sg[kMaxHistory];
+    T yr[kMaxHistory];
+    T coef[kMaxHistory];
+    T post[12];              // centre of mass, its velocity, angular velocity; warm start: R, y_cm
+    T* hs[kMaxHistory];      // history vectors s and y by age (newest first), set by first_loop
+    T* hy[kMaxHistory];
+    T aq[kMaxHistory];       // alpha_i and alpha_i - beta_i by age
+    T cq[kMaxHistory];
     long long item;          // work item handed to the block
     unsigned long long mbar; // tensor-core path: MMA completion barrier
     unsigned need[16];       // tensor-core path: request flags of the cluster's blocks
@@ -63,35 +120,35 @@ struct CellShared {
     int accept;
     int push;
 };
-static_assert(sizeof(CellShared) <= kFixedSmem - 8192, "CellShared does not fit");
+static_assert(sizeof(CellShared<double>) <= kFixedSmem - 8192, "CellShared does not fit");
 
-// A block-wide scalar for the solver's type: the FP64 value for the FP64 path, its
-// FP32 copy (written once by thread 0) otherwise, so that the FP32 path's threads
-// do no FP64 conversion.
 template <typename T>
-__device__ __forceinline__ T bcast(double d, float f)
+__device__ __forceinline__ CellShared<T>* cell_shared(unsigned char* smem)
+{
+    return reinterpret_cast<CellShared<T>*>(smem + 8192);
+}
+
+// A solver parameter in the solver's type (FP32 copies are set on the host).
+template <typename T>
+__device__ __forceinline__ T prm(double d, float f)
 {
     if constexpr (sizeof(T) == 8) return d;
     else return f;
-}
-
-__device__ __forceinline__ CellShared* cell_shared(unsigned char* smem)
-{
-    return reinterpret_cast<CellShared*>(smem + 8192);
 }
 
 // Sums K compensated accumulators over the block.  Thread 0 writes the totals to
 // sh->out[] and then runs epi(sh) before the closing barrier, so every thread sees
 // the totals and whatever the epilogue derived from them.
 struct NoEpi {
-    __device__ __forceinline__ void operator()(CellShared*) const {}
+    template <typename S>
+    __device__ __forceinline__ void operator()(S*) const {}
 };
 
 template <typename T, int K, typename Epi = NoEpi>
 __device__ __forceinline__ void block_reduce(Acc<T> (&a)[K], unsigned char* smem, Epi epi = Epi())
 {
     T* red = reinterpret_cast<T*>(smem);  // [32 warps][K][2]
-    CellShared* sh = cell_shared(smem);
+    CellShared<T>* sh = cell_shared<T>(smem);
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
@@ -127,7 +184,10 @@ __device__ __forceinline__ void block_reduce(Acc<T> (&a)[K], unsigned char* smem
             }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) sh->out[k] = (double)b[k].hi + (double)b[k].lo;
+            for (int k = 0; k < K; ++k) {
+                sh->out[k] = b[k].hi;
+                sh->outlo[k] = b[k].lo;
+            }
             epi(sh);
         }
     }
@@ -141,7 +201,7 @@ __device__ __forceinline__ void block_reduce_cp(Acc<T> (&a)[KC], T (&p)[KP], uns
 {
     constexpr int W = 2 * KC + KP;
     T* red = reinterpret_cast<T*>(smem);  // [32 warps][W]
-    CellShared* sh = cell_shared(smem);
+    CellShared<T>* sh = cell_shared<T>(smem);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -191,9 +251,12 @@ __device__ __forceinline__ void block_reduce_cp(Acc<T> (&a)[KC], T (&p)[KP], uns
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < KC; ++k) sh->out[k] = (double)b[k].hi + (double)b[k].lo;
+            for (int k = 0; k < KC; ++k) {
+                sh->out[k] = b[k].hi;
+                sh->outlo[k] = b[k].lo;
+            }
 #pragma unroll
-            for (int k = 0; k < KP; ++k) sh->out[KC + k] = (double)q[k];
+            for (int k = 0; k < KP; ++k) sh->out[KC + k] = q[k];
             epi(sh);
         }
     }
@@ -205,7 +268,7 @@ template <typename T, int K, typename Epi = NoEpi>
 __device__ __forceinline__ void block_sum(T (&p)[K], unsigned char* smem, Epi epi = Epi())
 {
     T* red = reinterpret_cast<T*>(smem);
-    CellShared* sh = cell_shared(smem);
+    CellShared<T>* sh = cell_shared<T>(smem);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -226,11 +289,64 @@ __device__ __forceinline__ void block_sum(T (&p)[K], unsigned char* smem, Epi ep
             for (int k = 0; k < K; ++k) q[k] += __shfl_xor_sync(kFull, q[k], o);
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) sh->out[k] = (double)q[k];
+            for (int k = 0; k < K; ++k) sh->out[k] = q[k];
             epi(sh);
         }
     }
     __syncthreads();
+}
+
+// Four consecutive elements of a per-cell vector (3 n_pad values, n_pad a multiple of
+// 4, 16-byte aligned): one 16-byte access for FP32, two for FP64.
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&r)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *reinterpret_cast<const double2*>(p + 2);
+        r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&r)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+    } else {
+        *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(r[2], r[3]);
+    }
+}
+
+// Eight consecutive read-only values (32-byte aligned) through the non-coherent path.
+template <typename T>
+__device__ __forceinline__ void ldg8(const T* p, T (&r)[8])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+        r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w; r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 a = __ldg(reinterpret_cast<const double2*>(p) + q);
+            r[2 * q] = a.x;
+            r[2 * q + 1] = a.y;
+        }
+    }
+}
+
+// The eight one-ring indices of vertex i from the fixed-width table.
+__device__ __forceinline__ void ring8_indices(const unsigned short* t, int i, int (&j)[8])
+{
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(t) + i);
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) j[q] = (int)((w[q >> 1] >> (16 * (q & 1))) & 0xffffu);
 }
 
 template <typename T>

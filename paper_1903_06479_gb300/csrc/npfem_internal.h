@@ -19,8 +19,11 @@ constexpr int kNumBaseVecs = 10;  // XN U UT G GT GC UY D TRI WR, then S[m], Y[m
 constexpr int kMaxVecs = kNumBaseVecs + 2 * kMaxHistory;
 constexpr int kFixedSmem = 12288; // reduction scratch (8 KB) + per-cell scalars at the start of dynamic smem
 
-// Per-cell buffers.  All are 3 x n_pad values except TRI (9 values per triangle:
-// the gradient contributions of corners j and k and the area-weighted normal / 6).
+// Per-cell buffers.  All are 3 x n_pad values except TRI (rows of kTriRow values per
+// triangle: the gradient contributions of corners j and k and the area-weighted
+// normal / 6, padded to 12 for 16-byte accesses).
+constexpr int kTriRow = 12;
+
 enum Vec { V_XN = 0, V_U = 1, V_UT = 2, V_G = 3, V_GT = 4, V_GC = 5, V_UY = 6, V_D = 7, V_TRI = 8, V_WR = 9, V_SBASE = 10 };
 
 enum Contraction { CONTRACT_SIMT = 0, CONTRACT_TC_TF32 = 1, CONTRACT_TC_BF16 = 2 };
@@ -45,6 +48,15 @@ struct TopoDev {
     const T* ring_ct;            // [nnz] weight of vertex i in the ring of its neighbour j
     const int* inc_ptr;          // [n + 1] vertex -> incident triangles
     const unsigned* inc_idx;     // [3 nt] (triangle << 2) | corner
+    // Fixed-width one-rings (k8 = 1: every one-ring is a single cycle of at most 8):
+    // vertex i's neighbours r_0 .. r_{v-1} in cyclic order, so that incident triangle
+    // q of i is (i, r_q, r_{q+1 mod v}); entries past v hold i itself with weight 0.
+    // tri[t].w then packs, 3 bits per corner, the slot q of each corner in its
+    // vertex's ring, where the triangle pass writes the corner's gradient.
+    int k8;
+    const unsigned short* ring8_idx;  // [n][8]
+    const T* ring8_c;                 // [n][8]
+    const T* ring8_ct;                // [n][8]
     const T* ainv;               // [n_pad][n_pad] A^-1 in T (zero padding)
     const void* ainv_lp;         // A^-1 for the tensor-core contraction (bf16 or tf32-rounded fp32)
     const int* h_ptr;            // L (CSR, fp32) for the refinement residual q - H~ r
@@ -57,7 +69,8 @@ struct TopoDev {
     T C, B, Dsk, kvol;           // material
     T h, inv_h2, inertia_scale;  // time step; inertia_scale = 1 + h alpha_D
     T kappa, lbar, inv_lbar;
-    double V0;
+    double V0;                   // rest volume
+    T V0hi, V0lo;                // V0 as an unevaluated sum of two T
 };
 
 // One mesh topology inside one launch.
@@ -74,11 +87,28 @@ struct GroupDesc {
 struct SolverParams {
     int lbfgs_m, max_iter, max_halvings, fixed_alpha;
     double tol, c1, c2, armijo_noise;
+    float tolf, c1f, c2f, armijo_noisef;  // FP32 copies for the FP32 path
     int mode;         // 0 = time step, 1 = objective/gradient evaluation
     int contraction;  // Contraction
     int cluster;      // tensor-core path: blocks per cluster (= row blocks of A^-1)
     int refine;       // tensor-core path: refinement sweeps (0 or 1)
 };
+
+inline void set_solver_params(SolverParams* p, const npfem_opts& o)
+{
+    p->lbfgs_m = o.lbfgs_m;
+    p->max_iter = o.max_iter;
+    p->max_halvings = o.max_halvings;
+    p->fixed_alpha = o.fixed_alpha;
+    p->tol = o.tol;
+    p->c1 = o.c1;
+    p->c2 = o.c2;
+    p->armijo_noise = o.armijo_noise;
+    p->tolf = (float)o.tol;
+    p->c1f = (float)o.c1;
+    p->c2f = (float)o.c2;
+    p->armijo_noisef = (float)o.armijo_noise;
+}
 
 template <typename T>
 struct LaunchArgs {
@@ -150,23 +180,31 @@ constexpr int kTcMaxVerts = 960;
 int set_error(int code, const std::string& msg);
 
 // Places the per-cell buffers: shared memory in priority order while they fit (the
-// randomly gathered ones first), the rest in a per-block global slot.  smem offsets
+// randomly gathered ones first; GC first of all with gc_first), the rest in a
+// per-block global slot.  smem offsets
 // start at base_off.  Returns the smem bytes used in g->smem_bytes.
 template <typename T>
 inline void place_vectors(GroupDesc<T>* g, int n_pad, int nt, int m, int smem_budget, long long* slot_bytes,
-                          int base_off = 0)
+                          int base_off = 0, bool gc_first = false)
 {
     const int vb = 3 * n_pad * (int)sizeof(T);
-    // TRI also serves as the contraction's scratch (max(32 warps, row tiles) x 384
+    // TRI (per-triangle rows, or per-vertex corner-gradient slots with fixed-width
+    // rings) also serves as the contraction's scratch (max(32 warps, row tiles) x 384
     // floats) and holds the warm start's normalised features ([n rounded to 16][16] floats)
-    const int tri_bytes = 9 * nt * (int)sizeof(T);
+    const int tri_bytes = kTriRow * nt * (int)sizeof(T);
     const int ctr_bytes = (((n_pad + 127) / 128) > 32 ? ((n_pad + 127) / 128) : 32) * 384 * 4;
     const int ws_bytes = ((n_pad + 15) & ~15) * 16 * 4;
+    const int slot_bytes8 = 24 * n_pad * (int)sizeof(T);  // [8 slots][3][n_pad] corner gradients
     int tb = tri_bytes > ctr_bytes ? tri_bytes : ctr_bytes;
+    tb = tb > slot_bytes8 ? tb : slot_bytes8;
     tb = ((tb > ws_bytes ? tb : ws_bytes) + 15) & ~15;
     int order[kMaxVecs], nv = 0;
     const int base[kNumBaseVecs] = {V_XN, V_U, V_UT, V_TRI, V_WR, V_G, V_GT, V_GC, V_UY, V_D};
-    for (int q = 0; q < kNumBaseVecs; ++q) order[nv++] = base[q];
+    // the tensor-core kernel writes contraction results into GC through distributed
+    // shared memory, so it needs GC in shared memory
+    if (gc_first) order[nv++] = V_GC;
+    for (int q = 0; q < kNumBaseVecs; ++q)
+        if (!(gc_first && base[q] == V_GC)) order[nv++] = base[q];
     for (int q = 0; q < m; ++q) {
         order[nv++] = V_SBASE + q;
         order[nv++] = V_SBASE + m + q;

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) ws_features_kernel(const TopoDev<float> t
     float* Y = reinterpret_cast<float*>(smem + kFixedSmem);
     float* D = Y + 3 * np;
     float* UY = D + 3 * np;
-    CellShared* sh = cell_shared(smem);
+    CellShared<float>* sh = cell_shared<float>(smem);
     const float h = tp.h, inv_ms = 1.f / tp.inertia_scale;
     for (int cell = blockIdx.x; cell < n_cells; cell += gridDim.x) {
         const long long so = (long long)cell * 3 * n;
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) ws_features_kernel(const TopoDev<float> t
         ws_frame(tp, Y, D, smem);
         float R[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) R[q] = sh->postf[q];
+        for (int q = 0; q < 9; ++q) R[q] = sh->post[q];
         for (int i = tid; i < n; i += NT) {
             float ft[kMlpIn];
             ws_vertex_features(tp, D, f + so, i, R, ft);
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(512, 2) ws_increment_kernel(const TopoDev<floa
     float* D = Y + 3 * np;
     float* UY = D + 3 * np;
     float* Xs = UY + 3 * np;  // [n16][16] normalised features
-    CellShared* sh = cell_shared(smem);
+    CellShared<float>* sh = cell_shared<float>(smem);
     const float h = tp.h, inv_ms = 1.f / tp.inertia_scale;
     const float* P = tp.mlp;
     for (int cell = blockIdx.x; cell < n_cells; cell += gridDim.x) {
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(512, 2) ws_increment_kernel(const TopoDev<floa
         ws_frame(tp, Y, D, smem);
         float R[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) R[q] = sh->postf[q];
+        for (int q = 0; q < 9; ++q) R[q] = sh->post[q];
         for (int i = tid; i < n16; i += NT) {
             float ft[kMlpIn];
             if (i < n) ws_vertex_features(tp, D, f + so, i, R, ft);

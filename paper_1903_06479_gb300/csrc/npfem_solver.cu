@@ -58,26 +58,29 @@ __device__ __forceinline__ T sl2_t(T e1, T e2)
     return t;
 }
 
-// Volume of the cell at x_n in local coordinates: V = sum_t X_i . (E1 x E2) / 6.
+// Triangle t's corner gradients (row: corner j, corner k, normal share / 3, padding)
+// into the buffer pass 2 gathers: with fixed-width rings, into the slots of the
+// three vertices (corner i gets minus the other two; the volume gradient is formed
+// from the ring in pass 2); otherwise the row itself.
 template <typename T>
-__device__ void volume_at_xn(const TopoDev<T>& tp, const T* XN, unsigned char* smem)
+__device__ __forceinline__ void store_corners(const TopoDev<T>& tp, T* TRI, int t, ushort4 tv, const T (&row)[kTriRow])
 {
-    const int np = tp.n_pad;
-    Acc<T> acc[1];
-    for (int t = threadIdx.x; t < tp.nt; t += blockDim.x) {
-        const ushort4 tv = __ldg(&tp.tri[t]);
-        T Xi[3], E1[3], E2[3];
+    if (tp.k8) {
+        const int np = tp.n_pad;
+        const unsigned sl = tv.w;
+        const int si = sl & 7u, sj = (sl >> 3) & 7u, sk = (sl >> 6) & 7u;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            Xi[c] = XN[c * np + tv.x];
-            E1[c] = XN[c * np + tv.y] - Xi[c];
-            E2[c] = XN[c * np + tv.z] - Xi[c];
+            TRI[(3 * si + c) * np + tv.x] = -(row[c] + row[3 + c]);
+            TRI[(3 * sj + c) * np + tv.y] = row[c];
+            TRI[(3 * sk + c) * np + tv.z] = row[3 + c];
         }
-        const T cx = E1[1] * E2[2] - E1[2] * E2[1], cy = E1[2] * E2[0] - E1[0] * E2[2],
-                cz = E1[0] * E2[1] - E1[1] * E2[0];
-        acc[0].add(Xi[0] * cx + Xi[1] * cy + Xi[2] * cz);
+    } else {
+        T* out = TRI + kTriRow * t;
+        st4(out, reinterpret_cast<const T(&)[4]>(row[0]));
+        st4(out + 4, reinterpret_cast<const T(&)[4]>(row[4]));
+        st4(out + 8, reinterpret_cast<const T(&)[4]>(row[8]));
     }
-    block_reduce<T, 1>(acc, smem, [](CellShared* sh) { sh->V = sh->out[0] / 6.0; });
 }
 
 // Objective g and gradient at x_n + U (Eq. GeneralizedObjectiveFunction and its
@@ -87,19 +90,21 @@ __device__ void volume_at_xn(const TopoDev<T>& tp, const T* XN, unsigned char* s
 // cell_shared(smem): E, its parts, V, residual r, rounding estimate of E, bad flag.
 // Vn is the volume at x_n (held by the caller).
 //
-// Gather form, no atomics: pass 1 writes each triangle's corner gradients and
-// area-weighted normal to TRI; pass 2 gathers them per vertex (vertex -> triangle
-// incidence) and computes the bending residual w_i r_i into WR; pass 3 gathers the
-// bending gradient from the neighbours' WR (transposed cotangent weights) and adds
-// the volume and inertia terms.  Every vertex is written by one thread only.
+// Gather form, no atomics: pass 1 writes each triangle's corner gradients to TRI
+// (with fixed-width rings into per-vertex slots, read back coalesced; otherwise as
+// per-triangle rows with the area-weighted normal, gathered through the vertex ->
+// triangle incidence); pass 2 sums them per vertex, forms the volume gradient and
+// the bending residual w_i r_i into WR; pass 3 gathers the bending gradient from the
+// neighbours' WR (transposed cotangent weights) and adds the volume and inertia
+// terms.  Every vertex is written by one thread only.
 // With kFirst, the same triangle pass also accumulates V(x_n) (left in sh->Vn) and
 // Vn is ignored.
 template <typename T, bool kFirst = false>
 __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T* UY, T* Gout, T* GC, T* TRI, T* WR,
-                         double Vn, unsigned char* smem)
+                         Pair<T> Vn, unsigned char* smem)
 {
     const int n = tp.n, np = tp.n_pad, tid = threadIdx.x, NT = blockDim.x;
-    CellShared* sh = cell_shared(smem);
+    CellShared<T>* sh = cell_shared<T>(smem);
     const T Cs = tp.C, Bs = tp.B, Ds = tp.Dsk;
     const T sixth = T(1) / T(6);
     Acc<T> ce[5];  // area, Skalak, bending energies; 6 dV; 6 V(x_n) (first evaluation only)
@@ -131,7 +136,6 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
             e1[c] = E1[c] + d1[c];
             e2[c] = E2[c] + d2[c];
         }
-        T* out = TRI + 9 * t;
         if (kFirst)
             ce[4].add(Xi[0] * (E1[1] * E2[2] - E1[2] * E2[1]) + Xi[1] * (E1[2] * E2[0] - E1[0] * E2[2]) +
                       Xi[2] * (E1[0] * E2[1] - E1[1] * E2[0]));
@@ -159,10 +163,14 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
         cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
         if (!(s2 > T(1e-6) * s1) || !(s1 < T(1e30))) {
             pl[2] += T(1);
+            T row[kTriRow];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) out[c] = T(0);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) out[6 + c] = cr[c] * sixth;
+            for (int c = 0; c < 3; ++c) {
+                row[c] = row[3 + c] = T(0);
+                row[6 + c] = cr[c] * sixth;
+            }
+            row[9] = row[10] = row[11] = T(0);
+            store_corners(tp, TRI, t, tv, row);
             continue;
         }
         const T e1s = m1 / (s1 + T(1)), e2s = m2 / (s2 + T(1));
@@ -201,14 +209,17 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
         dcr[1] = (E1[2] * d2[0] - E1[0] * d2[2]) + (d1[2] * E2[0] - d1[0] * E2[2]) + (d1[2] * d2[0] - d1[0] * d2[2]);
         dcr[2] = (E1[0] * d2[1] - E1[1] * d2[0]) + (d1[0] * E2[1] - d1[1] * E2[0]) + (d1[0] * d2[1] - d1[1] * d2[0]);
         ce[3].add((Xi[0] * dcr[0] + Xi[1] * dcr[1] + Xi[2] * dcr[2]) + (Ui[0] * cr[0] + Ui[1] * cr[1] + Ui[2] * cr[2]));
+        T row[kTriRow];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T G0 = F0[c] * K00 + F1[c] * K01;
             const T G1 = F0[c] * K01 + F1[c] * K11;
-            out[c] = G0 * Di0 + G1 * Di1;      // corner j
-            out[3 + c] = G0 * Di2 + G1 * Di3;  // corner k (corner i gets minus both)
-            out[6 + c] = cr[c] * sixth;        // share of the area-weighted normal / 3
+            row[c] = G0 * Di0 + G1 * Di1;      // corner j
+            row[3 + c] = G0 * Di2 + G1 * Di3;  // corner k (corner i gets minus both)
+            row[6 + c] = cr[c] * sixth;        // share of the area-weighted normal / 3
         }
+        row[9] = row[10] = row[11] = T(0);
+        store_corners(tp, TRI, t, tv, row);
     }
     __syncthreads();
 
@@ -224,16 +235,84 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
             continue;
         }
         T g[3] = {T(0), T(0), T(0)}, gc[3] = {T(0), T(0), T(0)};
-        const int b0 = __ldg(&tp.inc_ptr[i]), b1 = __ldg(&tp.inc_ptr[i + 1]);
-        for (int q = b0; q < b1; ++q) {
-            const unsigned e = __ldg(&tp.inc_idx[q]);
-            const T* P = TRI + 9 * (e >> 2);
-            const unsigned corner = e & 3u;
+        int jr[8];
+        int val = 0;
+        if (tp.k8) {
+            // the corner gradients of the vertex's triangles, one slot per ring entry
+            ring8_indices(tp.ring8_idx, i, jr);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T gj = P[c], gk = P[3 + c];
-                g[c] += corner == 1u ? gj : (corner == 2u ? gk : -(gj + gk));
-                gc[c] += P[6 + c];
+            for (int q = 0; q < 8; ++q) val += jr[q] != i;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < val)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) g[c] += TRI[(3 * q + c) * np + i];
+        } else {
+            const int b0 = __ldg(&tp.inc_ptr[i]), b1 = __ldg(&tp.inc_ptr[i + 1]);
+            for (int q = b0; q < b1; ++q) {
+                const unsigned e = __ldg(&tp.inc_idx[q]);
+                const T* P = TRI + kTriRow * (e >> 2);
+                const unsigned corner = e & 3u;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T gj = P[c], gk = P[3 + c];
+                    g[c] += corner == 1u ? gj : (corner == 2u ? gk : -(gj + gk));
+                    gc[c] += P[6 + c];
+                }
+            }
+        }
+        T dfn[3] = {T(0), T(0), T(0)}, dfu[3] = {T(0), T(0), T(0)};
+        T Xi[3], Ui[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Xi[c] = XN[c * np + i];
+            Ui[c] = U[c * np + i];
+        }
+        if (tp.k8) {
+            // bending: delta_f = sum_q c_q (x_{r_q} - x_i); volume gradient: one sixth of
+            // the sum of e_q x e_{q+1} over the incident triangles (e_q = x_{r_q} - x_i)
+            T cw[8];
+            ldg8(tp.ring8_c + 8 * i, cw);
+            T e0[3] = {T(0), T(0), T(0)}, ep[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q < val) {
+                    T ed[3], eu[3], ee[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        ed[c] = XN[c * np + jr[q]] - Xi[c];
+                        eu[c] = U[c * np + jr[q]] - Ui[c];
+                        dfn[c] += cw[q] * ed[c];
+                        dfu[c] += cw[q] * eu[c];
+                        ee[c] = ed[c] + eu[c];
+                    }
+                    if (q == 0) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) e0[c] = ee[c];
+                    } else {
+                        gc[0] += ep[1] * ee[2] - ep[2] * ee[1];
+                        gc[1] += ep[2] * ee[0] - ep[0] * ee[2];
+                        gc[2] += ep[0] * ee[1] - ep[1] * ee[0];
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ep[c] = ee[c];
+                }
+            }
+            gc[0] += ep[1] * e0[2] - ep[2] * e0[1];
+            gc[1] += ep[2] * e0[0] - ep[0] * e0[2];
+            gc[2] += ep[0] * e0[1] - ep[1] * e0[0];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gc[c] *= sixth;
+        } else {
+            const int r0 = __ldg(&tp.ring_ptr[i]), r1 = __ldg(&tp.ring_ptr[i + 1]);
+            for (int q = r0; q < r1; ++q) {
+                const int jn = __ldg(&tp.ring_idx[q]);
+                const T cq = __ldg(&tp.ring_c[q]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dfn[c] += cq * (XN[c * np + jn] - Xi[c]);
+                    dfu[c] += cq * (U[c * np + jn] - Ui[c]);
+                }
             }
         }
 #pragma unroll
@@ -242,24 +321,6 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
             GC[c * np + i] = gc[c];
         }
         pl[0] += gc[0] * gc[0] + gc[1] * gc[1] + gc[2] * gc[2];
-
-        const int r0 = __ldg(&tp.ring_ptr[i]), r1 = __ldg(&tp.ring_ptr[i + 1]);
-        T dfn[3] = {T(0), T(0), T(0)}, dfu[3] = {T(0), T(0), T(0)};
-        T Xi[3], Ui[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Xi[c] = XN[c * np + i];
-            Ui[c] = U[c * np + i];
-        }
-        for (int q = r0; q < r1; ++q) {
-            const int jn = __ldg(&tp.ring_idx[q]);
-            const T cq = __ldg(&tp.ring_c[q]);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                dfn[c] += cq * (XN[c * np + jn] - Xi[c]);
-                dfu[c] += cq * (U[c * np + jn] - Ui[c]);
-            }
-        }
         const T df[3] = {dfn[0] + dfu[0], dfn[1] + dfu[1], dfn[2] + dfu[2]};
         const T nf = sqrt(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
         const T ng = __ldg(&tp.dg_norm[i]);
@@ -285,23 +346,23 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
 #pragma unroll
         for (int c = 0; c < 3; ++c) WR[c * np + i] = w * r[c];
     }
-    const double kvol = (double)tp.kvol, V0 = tp.V0;
-    block_reduce_cp<T, 5, 3>(ce, pl, smem, [=](CellShared* s) {
-        s->Earea = s->out[0];
-        s->Esk = s->out[1];
-        s->Ebend = s->out[2];
-        const double vn = kFirst ? s->out[4] / 6.0 : Vn;
+    const T kvol = tp.kvol;
+    const Pair<T> V0 = {tp.V0hi, tp.V0lo};
+    block_reduce_cp<T, 5, 3>(ce, pl, smem, [=](CellShared<T>* s) {
+        s->Earea = {s->out[0], s->outlo[0]};
+        s->Esk = {s->out[1], s->outlo[1]};
+        s->Ebend = {s->out[2], s->outlo[2]};
+        const Pair<T> vn = kFirst ? pair_div6(s->out[4], s->outlo[4]) : Vn;
         s->Vn = vn;
-        s->V = vn + s->out[3] / 6.0;
-        const double Cv = s->V - V0;
-        const T inv = T(1) / (T)s->out[5];
-        s->Evol = 0.5 * kvol * Cv * Cv * (double)inv;
-        s->volc = kvol * Cv * (double)inv;
-        s->volcf = (float)s->volc;
+        s->V = pair_add(vn, pair_div6(s->out[3], s->outlo[3]));
+        const T Cv = pair_diff(s->V, V0);
+        const T inv = T(1) / s->out[5];
+        s->Evol = T(0.5) * kvol * Cv * Cv * inv;
+        s->volc = kvol * Cv * inv;
         s->noise = s->out[6];
-        s->bad = s->out[7] != 0.0;
+        s->bad = s->out[7] != T(0);
     });
-    const T volc = bcast<T>(sh->volc, sh->volcf);
+    const T volc = sh->volc;
 
     // ---- pass 3: bending gather, volume and inertia (M~ = (1 + h alpha_D) M), residual
     const T ms = tp.inertia_scale * tp.inv_h2, h2 = tp.h * tp.h;
@@ -310,16 +371,29 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
     for (int i = tid; i < n; i += NT) {
         const T m = __ldg(&tp.mass[i]);
         const T hm = h2 * __ldg(&tp.inv_mass[i]);
-        const int r0 = __ldg(&tp.ring_ptr[i]), r1 = __ldg(&tp.ring_ptr[i + 1]);
         const T cs = __ldg(&tp.csum[i]);
         T gb[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) gb[c] = -cs * WR[c * np + i];
-        for (int q = r0; q < r1; ++q) {
-            const int jn = __ldg(&tp.ring_idx[q]);
-            const T ct = __ldg(&tp.ring_ct[q]);
+        if (tp.k8) {
+            int jr[8];
+            T cw[8];
+            ring8_indices(tp.ring8_idx, i, jr);
+            ldg8(tp.ring8_ct + 8 * i, cw);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gb[c] += ct * WR[c * np + jn];
+            for (int q = 0; q < 8; ++q) {
+                if (jr[q] == i) continue;  // padding
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gb[c] += cw[q] * WR[c * np + jr[q]];
+            }
+        } else {
+            const int r0 = __ldg(&tp.ring_ptr[i]), r1 = __ldg(&tp.ring_ptr[i + 1]);
+            for (int q = r0; q < r1; ++q) {
+                const int jn = __ldg(&tp.ring_idx[q]);
+                const T ct = __ldg(&tp.ring_ct[q]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gb[c] += ct * WR[c * np + jn];
+            }
         }
         T g2 = T(0), ei = T(0);
 #pragma unroll
@@ -334,12 +408,15 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
         pr[0] += hm * hm * g2;
     }
     const T inv_n = T(1) / T(n), inv_lbar = tp.inv_lbar;
-    const double uT = Unit<T>::u;
-    block_reduce_cp<T, 1, 1>(ci, pr, smem, [=](CellShared* s) {
-        s->Ein = s->out[0];
-        s->E = s->Ein + s->Earea + s->Esk + s->Ebend + s->Evol;
-        s->res = (double)(sqrt((T)s->out[1] * inv_n) * inv_lbar);
-        s->noise = 4.0 * uT * (s->noise + 2.0 * s->Ein);
+    const T uT = T(Unit<T>::u);
+    block_reduce_cp<T, 1, 1>(ci, pr, smem, [=](CellShared<T>* s) {
+        s->Ein = {s->out[0], s->outlo[0]};
+        s->E = pair_add(pair_add(pair_add(pair_add(s->Ein, s->Earea), s->Esk), s->Ebend), s->Evol);
+        const T res = sqrt(s->out[1] * inv_n) * inv_lbar;
+        s->res = res;
+        s->noise = T(4) * uT * (s->noise + T(2) * s->Ein.hi);
+        // non-finite energy or residual marks the evaluation bad
+        if (!isfinite(s->E.hi) || !isfinite(res)) s->bad = 1;
     });
 }
 
@@ -460,11 +537,12 @@ struct CellSolver {
     const GroupDesc<T>* gd;
     unsigned char* smem;
     char* slot;
-    CellShared* sh;
+    CellShared<T>* sh;
     T *XN, *u, *ut, *g, *gt, *GCv, *UYv, *Dv, *TRIv, *WRv;
     long long so, item;
     int M, head, count, iters, evals, status;
-    double E, noiseE, res, Vlast, Vn, gdv;
+    Pair<T> E, Vlast, Vn;
+    T noiseE, res, gdv;
     bool nonfinite;
 
     __device__ const TopoDev<T>& tp() const { return gd->topo; }
@@ -475,7 +553,7 @@ struct CellSolver {
         a = &la;
         gd = &g_;
         smem = sm;
-        sh = cell_shared(sm);
+        sh = cell_shared<T>(sm);
         slot = la.scratch ? la.scratch + (long long)blockIdx.x * la.slot_bytes : nullptr;
         XN = vec_ptr(g_, sm, slot, V_XN);
         u = vec_ptr(g_, sm, slot, V_U);
@@ -536,7 +614,7 @@ struct CellSolver {
             ws_frame(T_, ut, WRv, smem);
             T R[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) R[q] = sh->postf[q];
+            for (int q = 0; q < 9; ++q) R[q] = sh->post[q];
             const T* F = a->f + so;
             const float* P = T_.mlp;
             // normalised features of every vertex (one thread each) into the idle
@@ -578,13 +656,14 @@ struct CellSolver {
             // keep the learned guess only if it lowers g: evaluate at y (trial buffers) first
             for (int e = tid; e < N3; e += NT) ut[e] = UYv[e];
             __syncthreads();
-            evaluate<T, true>(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, 0.0, smem);
+            evaluate<T, true>(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, Pair<T>{T(0), T(0)}, smem);
             Vn = sh->Vn;
-            const double Ey = sh->E, ny = sh->noise, ry = sh->res, Vy = sh->V;
+            const Pair<T> Ey = sh->E, Vy = sh->V;
+            const T ny = sh->noise, ry = sh->res;
             const bool by = sh->bad;
             evaluate<T, false>(T_, XN, u, UYv, g, GCv, TRIv, WRv, Vn, smem);
             evals = 2;
-            if (!(sh->E <= Ey) && !by) {
+            if (!(pair_diff(sh->E, Ey) <= T(0)) && !by) {
                 T* t1 = u; u = ut; ut = t1;
                 T* t2 = g; g = gt; gt = t2;
                 if (tid == 0) {
@@ -597,7 +676,7 @@ struct CellSolver {
                 __syncthreads();
             }
         } else {
-            evaluate<T, true>(T_, XN, u, UYv, g, GCv, TRIv, WRv, 0.0, smem);
+            evaluate<T, true>(T_, XN, u, UYv, g, GCv, TRIv, WRv, Pair<T>{T(0), T(0)}, smem);
             Vn = sh->Vn;
         }
         iters = 0;
@@ -611,8 +690,9 @@ struct CellSolver {
             }
             if (tid == 0) {
                 double* P = a->parts + 8 * item;
-                P[0] = sh->Ein; P[1] = sh->Earea; P[2] = sh->Esk; P[3] = sh->Ebend; P[4] = sh->Evol;
-                P[5] = sh->V; P[6] = sh->E; P[7] = sh->res;
+                P[0] = pair_f64(sh->Ein); P[1] = pair_f64(sh->Earea); P[2] = pair_f64(sh->Esk);
+                P[3] = pair_f64(sh->Ebend); P[4] = (double)sh->Evol;
+                P[5] = pair_f64(sh->V); P[6] = pair_f64(sh->E); P[7] = (double)sh->res;
             }
             __syncthreads();
             return false;
@@ -621,7 +701,7 @@ struct CellSolver {
         noiseE = sh->noise;
         res = sh->res;
         Vlast = sh->V;
-        nonfinite = sh->bad || !isfinite(sh->E) || !isfinite(sh->res);
+        nonfinite = sh->bad != 0;
         return true;
     }
 
@@ -629,7 +709,7 @@ struct CellSolver {
     __device__ bool wants_direction()
     {
         if (nonfinite) return false;
-        if (res <= a->p.tol) return false;
+        if (res <= prm<T>(a->p.tol, a->p.tolf)) return false;
         if (iters >= a->p.max_iter) {
             status = NPFEM_CELL_MAXITER;
             return false;
@@ -637,41 +717,111 @@ struct CellSolver {
         return true;
     }
 
-    // First loop of the two-loop recursion: q = g; alpha_i = rho_i s_i^T q;
-    // q -= alpha_i y_i (newest first).  q is left in Dv.
+    // History slot of the q-th newest pair.
+    __device__ int hslot(int q) const { return (head - 1 - q + M) % M; }
+
+    // First loop of the two-loop recursion (Nocedal & Wright Alg. 7.4), newest pair
+    // first, on scalars: with s_i^T g and the pairs' inner products s_i^T y_j kept up to
+    // date, alpha_i = rho_i (s_i^T g - sum_{j newer} alpha_j s_i^T y_j) on thread 0;
+    // one pass then forms q = g - sum_i alpha_i y_i in Dv.  Thread 0 also publishes the
+    // history vectors by age for the second loop and the line search.
     __device__ void first_loop()
     {
         const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x;
-        for (int e = tid; e < N3; e += NT) Dv[e] = g[e];
-        for (int q = 0; q < count; ++q) {
-            const int i = (head - 1 - q + M) % M;
-            const T* S = hist(V_SBASE + i);
-            const T* Y = hist(V_SBASE + M + i);
-            T s[1] = {T(0)};
-            for (int e = tid; e < N3; e += NT) s[0] += S[e] * Dv[e];
-            block_sum<T, 1>(s, smem, [=](CellShared* c) { c->alpha[i] = c->rho[i] * c->out[0]; });
-            const T al = (T)sh->alpha[i];
-            for (int e = tid; e < N3; e += NT) Dv[e] -= al * Y[e];
+        const int cnt = count;
+        if (cnt > 0) {
+            if (tid == 0) {
+                for (int q = 0; q < cnt; ++q) {
+                    const int i = hslot(q);
+                    sh->hs[q] = hist(V_SBASE + i);
+                    sh->hy[q] = hist(V_SBASE + M + i);
+                    T t = sh->sg[i];
+                    for (int p = 0; p < q; ++p) {
+                        const int j = hslot(p);
+                        t -= sh->alpha[j] * sh->SY[i][j];
+                    }
+                    const T al = sh->rho[i] * t;
+                    sh->alpha[i] = al;
+                    sh->aq[q] = al;
+                }
+            }
+            __syncthreads();
+        }
+        for (int e = 4 * tid; e < N3; e += 4 * NT) {
+            T d[4];
+            ld4(g + e, d);
+            for (int q = 0; q < cnt; ++q) {
+                T y[4];
+                ld4(sh->hy[q] + e, y);
+                const T al = sh->aq[q];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) d[k] -= al * y[k];
+            }
+            st4(Dv + e, d);
         }
         __syncthreads();
     }
 
-    // Second loop (oldest first) on r = H0 q held in GCv: beta = rho_i y_i^T r;
-    // r += s_i (alpha_i - beta); then d = -r into Dv and gdv = g^T d.
+    // Second loop (oldest pair first) on r = H0 q held in GCv: one block reduction gives
+    // y_i^T r for every pair; thread 0 runs beta_i = rho_i (y_i^T r + sum_{j older}
+    // (alpha_j - beta_j) s_j^T y_i); one pass forms d = -(r + sum_i (alpha_i - beta_i) s_i)
+    // in Dv together with gdv = g^T d.
     __device__ void second_loop()
     {
         const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x;
-        for (int q = count - 1; q >= 0; --q) {
-            const int i = (head - 1 - q + M) % M;
-            const T* S = hist(V_SBASE + i);
-            const T* Y = hist(V_SBASE + M + i);
-            T s[1] = {T(0)};
-            for (int e = tid; e < N3; e += NT) s[0] += Y[e] * GCv[e];
-            block_sum<T, 1>(s, smem, [=](CellShared* c) { c->out[1] = c->alpha[i] - c->rho[i] * c->out[0]; });
-            const T coef = (T)sh->out[1];
-            for (int e = tid; e < N3; e += NT) GCv[e] += S[e] * coef;
+        const int cnt = count, hd = head, Mm = M;
+        if (cnt > 0) {
+            T yr[kMaxHistory];
+#pragma unroll
+            for (int q = 0; q < kMaxHistory; ++q) yr[q] = T(0);
+            for (int e = 4 * tid; e < N3; e += 4 * NT) {
+                T r[4];
+                ld4(GCv + e, r);
+#pragma unroll
+                for (int q = 0; q < kMaxHistory; ++q) {
+                    if (q < cnt) {
+                        T y[4];
+                        ld4(sh->hy[q] + e, y);
+                        yr[q] += (y[0] * r[0] + y[1] * r[1]) + (y[2] * r[2] + y[3] * r[3]);
+                    }
+                }
+            }
+            block_sum<T, kMaxHistory>(yr, smem, [=](CellShared<T>* c) {
+                for (int q = cnt - 1; q >= 0; --q) {
+                    const int i = (hd - 1 - q + Mm) % Mm;
+                    c->yr[i] = c->out[q];
+                    T t = c->out[q];
+                    for (int p = cnt - 1; p > q; --p) {
+                        const int j = (hd - 1 - p + Mm) % Mm;
+                        t += c->coef[j] * c->SY[j][i];
+                    }
+                    const T cf = c->alpha[i] - c->rho[i] * t;
+                    c->coef[i] = cf;
+                    c->cq[q] = cf;
+                }
+            });
         }
-        negate_direction();
+        T s1[1] = {T(0)};
+        for (int e = 4 * tid; e < N3; e += 4 * NT) {
+            T r[4], gv[4];
+            ld4(GCv + e, r);
+            for (int q = 0; q < cnt; ++q) {
+                T sv[4];
+                ld4(sh->hs[q] + e, sv);
+                const T cf = sh->cq[q];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) r[k] += cf * sv[k];
+            }
+            ld4(g + e, gv);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                r[k] = -r[k];
+                s1[0] += gv[k] * r[k];
+            }
+            st4(Dv + e, r);
+        }
+        block_sum<T, 1>(s1, smem);
+        gdv = sh->out[0];
     }
 
     // d = -GCv into Dv, gdv = g^T d.
@@ -679,10 +829,16 @@ struct CellSolver {
     {
         const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x;
         T s[1] = {T(0)};
-        for (int e = tid; e < N3; e += NT) {
-            const T dv = -GCv[e];
-            Dv[e] = dv;
-            s[0] += g[e] * dv;
+        for (int e = 4 * tid; e < N3; e += 4 * NT) {
+            T r[4], gv[4];
+            ld4(GCv + e, r);
+            ld4(g + e, gv);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                r[k] = -r[k];
+                s[0] += gv[k] * r[k];
+            }
+            st4(Dv + e, r);
         }
         block_sum<T, 1>(s, smem);
         gdv = sh->out[0];
@@ -697,17 +853,24 @@ struct CellSolver {
     {
         const TopoDev<T>& T_ = tp();
         const int N3 = 3 * T_.n_pad, tid = threadIdx.x, NT = blockDim.x;
-        const double c1 = a->p.c1, c2 = a->p.c2, anoise = a->p.armijo_noise;
-        double alpha = 1.0;
-        T al = T(1);  // alpha in the working type (powers of two: exact)
+        const T c1 = prm<T>(a->p.c1, a->p.c1f), c2 = prm<T>(a->p.c2, a->p.c2f);
+        const T anoise = prm<T>(a->p.armijo_noise, a->p.armijo_noisef);
+        T alpha = T(1);
         bool accepted = false;
         for (int hv = 0; hv <= a->p.max_halvings; ++hv) {
-            for (int e = tid; e < N3; e += NT) ut[e] = u[e] + al * Dv[e];
+            for (int e = 4 * tid; e < N3; e += 4 * NT) {
+                T uv[4], dv[4];
+                ld4(u + e, uv);
+                ld4(Dv + e, dv);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) uv[k] += alpha * dv[k];
+                st4(ut + e, uv);
+            }
             __syncthreads();
             evaluate(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, Vn, smem);
             ++evals;
             if (tid == 0) {
-                const bool ok = !sh->bad && sh->E <= E + c1 * alpha * gdv + anoise * (sh->noise + noiseE);
+                const bool ok = !sh->bad && pair_diff(sh->E, E) <= c1 * alpha * gdv + anoise * (sh->noise + noiseE);
                 sh->accept = a->p.fixed_alpha || ok;
             }
             __syncthreads();
@@ -715,36 +878,90 @@ struct CellSolver {
                 accepted = true;
                 break;
             }
-            alpha *= 0.5;
-            al *= T(0.5);
+            alpha *= T(0.5);
         }
         if (!accepted) {
             status = NPFEM_CELL_LINESEARCH_FAIL;
             return false;
         }
         // history pair (s, y) = (x_{k+1} - x_k, grad_{k+1} - grad_k), kept when the
-        // curvature condition holds and s^T y > 0
+        // curvature condition holds and s^T y > 0.  The same pass gives s_j^T g_{k+1}
+        // for the stored pairs, which keeps the two-loop's inner products current:
+        // s_j^T y_new = s_j^T g_{k+1} - s_j^T g_k, and s_new^T y_j = alpha d^T y_j with
+        // d^T y_j = -(y_j^T r + sum_l (alpha_l - beta_l) s_l^T y_j) from the last
+        // second loop.
         if (M > 0) {
-            T acc[4] = {T(0), T(0), T(0), T(0)};  // s^T y, s^T s, y^T y, grad_new^T d
-            for (int e = tid; e < N3; e += NT) {
-                const T se = ut[e] - u[e], ye = gt[e] - g[e];
-                acc[0] += se * ye;
-                acc[1] += se * se;
-                acc[2] += ye * ye;
-                acc[3] += gt[e] * Dv[e];
+            const int cnt = count, hd = head, Mm = M;
+            T acc[5 + kMaxHistory];  // s^T y, s^T s, y^T y, g_new^T d, s^T g_new, s_j^T g_new
+#pragma unroll
+            for (int q = 0; q < 5 + kMaxHistory; ++q) acc[q] = T(0);
+            for (int e = 4 * tid; e < N3; e += 4 * NT) {
+                T gn[4], go[4], un[4], uo[4], dv[4];
+                ld4(gt + e, gn);
+                ld4(g + e, go);
+                ld4(ut + e, un);
+                ld4(u + e, uo);
+                ld4(Dv + e, dv);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const T se = un[k] - uo[k], ye = gn[k] - go[k];
+                    acc[0] += se * ye;
+                    acc[1] += se * se;
+                    acc[2] += ye * ye;
+                    acc[3] += gn[k] * dv[k];
+                    acc[4] += se * gn[k];
+                }
+#pragma unroll
+                for (int q = 0; q < kMaxHistory; ++q) {
+                    if (q < cnt) {
+                        T sv[4];
+                        ld4(sh->hs[q] + e, sv);
+                        acc[5 + q] += (sv[0] * gn[0] + sv[1] * gn[1]) + (sv[2] * gn[2] + sv[3] * gn[3]);
+                    }
+                }
             }
-            const int hd = head;
-            const double gd0 = gdv;
-            block_sum<T, 4>(acc, smem, [=](CellShared* c) {
-                c->push = c->out[3] >= c2 * gd0 && c->out[0] > 1e-12 * sqrt(c->out[1] * c->out[2]);
-                if (c->push) c->rho[hd] = 1.0 / c->out[0];
+            const T gd0 = gdv, al = alpha;
+            block_sum<T, 5 + kMaxHistory>(acc, smem, [=](CellShared<T>* c) {
+                const T* o = c->out;
+                c->push = o[3] >= c2 * gd0 && o[0] > T(1e-12) * sqrt(o[1]) * sqrt(o[2]);
+                if (c->push) {
+                    T dy[kMaxHistory];
+                    for (int q = 0; q < cnt; ++q) {
+                        const int j = (hd - 1 - q + Mm) % Mm;
+                        T t = c->yr[j];
+                        for (int p = 0; p < cnt; ++p) {
+                            const int l = (hd - 1 - p + Mm) % Mm;
+                            t += c->coef[l] * c->SY[l][j];
+                        }
+                        dy[q] = -t;
+                    }
+                    for (int q = 0; q < cnt; ++q) {
+                        const int j = (hd - 1 - q + Mm) % Mm;
+                        if (j == hd) continue;  // the oldest pair, overwritten
+                        c->SY[hd][j] = al * dy[q];
+                        c->SY[j][hd] = o[5 + q] - c->sg[j];
+                    }
+                    c->SY[hd][hd] = o[0];
+                    c->rho[hd] = T(1) / o[0];
+                }
+                for (int q = 0; q < cnt; ++q) c->sg[(hd - 1 - q + Mm) % Mm] = o[5 + q];
+                if (c->push) c->sg[hd] = o[4];
             });
             if (sh->push) {
                 T* S = hist(V_SBASE + head);
                 T* Y = hist(V_SBASE + M + head);
-                for (int e = tid; e < N3; e += NT) {
-                    S[e] = ut[e] - u[e];
-                    Y[e] = gt[e] - g[e];
+                for (int e = 4 * tid; e < N3; e += 4 * NT) {
+                    T a4[4], b4[4];
+                    ld4(ut + e, a4);
+                    ld4(u + e, b4);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) a4[k] -= b4[k];
+                    st4(S + e, a4);
+                    ld4(gt + e, a4);
+                    ld4(g + e, b4);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) a4[k] -= b4[k];
+                    st4(Y + e, a4);
                 }
                 head = (head + 1) % M;
                 count = count < M ? count + 1 : M;
@@ -757,7 +974,7 @@ struct CellSolver {
         res = sh->res;
         Vlast = sh->V;
         ++iters;
-        nonfinite = sh->bad || !isfinite(sh->E) || !isfinite(sh->res);
+        nonfinite = sh->bad != 0;
         __syncthreads();
         return true;
     }
@@ -798,48 +1015,45 @@ struct CellSolver {
             }
         }
         const bool nf = nonfinite;
-        block_reduce<T, 16>(ps, smem, [=](CellShared* s) {
-            double* o = s->out;
-            double* P = s->post;
-            for (int q = 0; q < 9; ++q) {
-                P[q] = 0.0;
-                s->postf[q] = 0.f;
-            }
+        block_reduce<T, 16>(ps, smem, [=](CellShared<T>* s) {
+            const T* o = s->out;
+            T* P = s->post;
+            for (int q = 0; q < 9; ++q) P[q] = T(0);
             if (nf) return;
-            const double Mt = o[0];
-            double xc[3], vc[3];
+            const T Mt = o[0];
+            T xc[3], vc[3];
             for (int c = 0; c < 3; ++c) {
                 xc[c] = o[1 + c] / Mt;
                 vc[c] = o[4 + c] / Mt;
             }
             // angular momentum and inertia tensor about the centre of mass
-            const double L0 = o[7] - Mt * (xc[1] * vc[2] - xc[2] * vc[1]);
-            const double L1 = o[8] - Mt * (xc[2] * vc[0] - xc[0] * vc[2]);
-            const double L2 = o[9] - Mt * (xc[0] * vc[1] - xc[1] * vc[0]);
-            const double Sxx = o[10] - Mt * xc[0] * xc[0], Syy = o[11] - Mt * xc[1] * xc[1],
-                         Szz = o[12] - Mt * xc[2] * xc[2];
-            const double Sxy = o[13] - Mt * xc[0] * xc[1], Sxz = o[14] - Mt * xc[0] * xc[2],
-                         Syz = o[15] - Mt * xc[1] * xc[2];
-            const double I00 = Syy + Szz, I11 = Sxx + Szz, I22 = Sxx + Syy;
-            const double I01 = -Sxy, I02 = -Sxz, I12 = -Syz;
-            const double c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
-            const double c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
-            const double det = I00 * c00 + I01 * c01 + I02 * c02;
+            const T L0 = o[7] - Mt * (xc[1] * vc[2] - xc[2] * vc[1]);
+            const T L1 = o[8] - Mt * (xc[2] * vc[0] - xc[0] * vc[2]);
+            const T L2 = o[9] - Mt * (xc[0] * vc[1] - xc[1] * vc[0]);
+            const T Sxx = o[10] - Mt * xc[0] * xc[0], Syy = o[11] - Mt * xc[1] * xc[1],
+                    Szz = o[12] - Mt * xc[2] * xc[2];
+            const T Sxy = o[13] - Mt * xc[0] * xc[1], Sxz = o[14] - Mt * xc[0] * xc[2],
+                    Syz = o[15] - Mt * xc[1] * xc[2];
+            const T I00 = Syy + Szz, I11 = Sxx + Szz, I22 = Sxx + Syy;
+            const T I01 = -Sxy, I02 = -Sxz, I12 = -Syz;
+            const T c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
+            const T c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
+            const T det = I00 * c00 + I01 * c01 + I02 * c02;
+            const T idet = T(1) / det;
             for (int c = 0; c < 3; ++c) {
                 P[c] = xc[c];
                 P[3 + c] = vc[c];
             }
-            P[6] = (c00 * L0 + c01 * L1 + c02 * L2) / det;
-            P[7] = (c01 * L0 + c11 * L1 + c12 * L2) / det;
-            P[8] = (c02 * L0 + c12 * L1 + c22 * L2) / det;
-            for (int q = 0; q < 9; ++q) s->postf[q] = (float)P[q];
+            P[6] = (c00 * L0 + c01 * L1 + c02 * L2) * idet;
+            P[7] = (c01 * L0 + c11 * L1 + c12 * L2) * idet;
+            P[8] = (c02 * L0 + c12 * L1 + c22 * L2) * idet;
         });
         T xc[3], vc[3], w[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            xc[c] = bcast<T>(sh->post[c], sh->postf[c]);
-            vc[c] = bcast<T>(sh->post[3 + c], sh->postf[3 + c]);
-            w[c] = bcast<T>(sh->post[6 + c], sh->postf[6 + c]);
+            xc[c] = sh->post[c];
+            vc[c] = sh->post[3 + c];
+            w[c] = sh->post[6 + c];
         }
         const T kap = T_.kappa;
         T* x = a->x + so;
@@ -865,8 +1079,8 @@ struct CellSolver {
             st.evaluations = evals;
             st.status = status;
             st.residual = (float)res;
-            st.objective = E;
-            st.volume = Vlast;
+            st.objective = pair_f64(E);
+            st.volume = pair_f64(Vlast);
             a->stats[item] = st;
         }
         __syncthreads();
@@ -877,7 +1091,7 @@ struct CellSolver {
 template <typename T>
 __device__ __forceinline__ long long next_item(const LaunchArgs<T>& a, unsigned char* smem)
 {
-    CellShared* sh = cell_shared(smem);
+    CellShared<T>* sh = cell_shared<T>(smem);
     if (threadIdx.x == 0) sh->item = (long long)atomicAdd(&a.work[0], 1u);
     __syncthreads();
     const long long it = sh->item;
@@ -1096,7 +1310,7 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
     extern __shared__ __align__(1024) unsigned char smem[];
     const GroupDesc<T>& gd = a.g[0];
     const TopoDev<T>& tp = gd.topo;
-    CellShared* sh = cell_shared(smem);
+    CellShared<T>* sh = cell_shared<T>(smem);
     unsigned char* bbuf = smem + kFixedSmem;  // B operand: NCOL rows x kpad BF16
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t rank = tc::cta_rank(), cs = (uint32_t)a.p.cluster;

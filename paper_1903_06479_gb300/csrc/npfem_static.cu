@@ -108,14 +108,7 @@ int run_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells, 
     a.work = reinterpret_cast<unsigned int*>(base);
     a.scratch = slot > 0 ? base + NPFEM_STATIC_COUNTER_BYTES : nullptr;
     a.slot_bytes = slot;
-    a.p.lbfgs_m = h0->opts.lbfgs_m;
-    a.p.max_iter = h0->opts.max_iter;
-    a.p.max_halvings = h0->opts.max_halvings;
-    a.p.fixed_alpha = h0->opts.fixed_alpha;
-    a.p.tol = h0->opts.tol;
-    a.p.c1 = h0->opts.c1;
-    a.p.c2 = h0->opts.c2;
-    a.p.armijo_noise = h0->opts.armijo_noise;
+    set_solver_params(&a.p, h0->opts);
     a.p.mode = 0;
     a.p.contraction = CONTRACT_SIMT;
 

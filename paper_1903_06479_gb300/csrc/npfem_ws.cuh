@@ -201,13 +201,13 @@ __device__ inline void polar_rotation(const S (&A)[9], S (&R)[9])
 }
 
 // Best-fit frame of one cell at local positions Y ([3][n_pad]): R (row-major) and
-// y_cm go to sh->postf[0..8] and sh->postf[9..11]; the rest-frame displacements d go
+// y_cm go to sh->post[0..8] and sh->post[9..11]; the rest-frame displacements d go
 // to D ([3][n_pad], zero padding).  Block-cooperative.
 template <typename T>
 __device__ void ws_frame(const TopoDev<T>& tp, const T* Y, T* D, unsigned char* smem)
 {
     const int n = tp.n, np = tp.n_pad, tid = threadIdx.x, NT = blockDim.x;
-    CellShared* sh = cell_shared(smem);
+    CellShared<T>* sh = cell_shared<T>(smem);
     // plain sums: the frame only needs the working precision
     T acc[13] = {};  // sum m y Xc^T (9), sum m y (3), sum m
     for (int i = tid; i < n; i += NT) {
@@ -226,18 +226,19 @@ __device__ void ws_frame(const TopoDev<T>& tp, const T* Y, T* D, unsigned char* 
         for (int a = 0; a < 3; ++a) acc[9 + a] += m * y[a];
         acc[12] += m;
     }
-    block_sum<T, 13>(acc, smem, [](CellShared* s) {
-        float A[9], R[9];
-        for (int q = 0; q < 9; ++q) A[q] = (float)s->out[q];
-        polar_rotation<float>(A, R);
-        for (int q = 0; q < 9; ++q) s->postf[q] = R[q];
-        for (int a = 0; a < 3; ++a) s->postf[9 + a] = (float)(s->out[9 + a] / s->out[12]);
+    block_sum<T, 13>(acc, smem, [](CellShared<T>* s) {
+        T A[9], R[9];
+        for (int q = 0; q < 9; ++q) A[q] = s->out[q];
+        polar_rotation<T>(A, R);
+        for (int q = 0; q < 9; ++q) s->post[q] = R[q];
+        const T im = T(1) / s->out[12];
+        for (int a = 0; a < 3; ++a) s->post[9 + a] = s->out[9 + a] * im;
     });
     T R[9], yc[3];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) R[q] = sh->postf[q];
+    for (int q = 0; q < 9; ++q) R[q] = sh->post[q];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) yc[a] = sh->postf[9 + a];
+    for (int a = 0; a < 3; ++a) yc[a] = sh->post[9 + a];
     for (int i = tid; i < np; i += NT) {
         if (i >= n) {
 #pragma unroll
@@ -261,11 +262,24 @@ __device__ __forceinline__ void ws_vertex_features(const TopoDev<T>& tp, const T
     const int n = tp.n, np = tp.n_pad;
     T lap[3] = {T(0), T(0), T(0)};
     const T di[3] = {D[i], D[np + i], D[2 * np + i]};
-    for (int q = tp.ring_ptr[i]; q < tp.ring_ptr[i + 1]; ++q) {
-        const int j = tp.ring_idx[q];
-        const T cq = tp.ring_c[q];
+    if (tp.k8) {
+        int jr[8];
+        T cw[8];
+        ring8_indices(tp.ring8_idx, i, jr);
+        ldg8(tp.ring8_c + 8 * i, cw);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) lap[c] += cq * (D[c * np + j] - di[c]);
+        for (int q = 0; q < 8; ++q) {
+            if (jr[q] == i) continue;  // padding
+#pragma unroll
+            for (int c = 0; c < 3; ++c) lap[c] += cw[q] * (D[c * np + jr[q]] - di[c]);
+        }
+    } else {
+        for (int q = tp.ring_ptr[i]; q < tp.ring_ptr[i + 1]; ++q) {
+            const int j = tp.ring_idx[q];
+            const T cq = tp.ring_c[q];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) lap[c] += cq * (D[c * np + j] - di[c]);
+        }
     }
     const T sc = tp.h * tp.h * tp.inv_mass[i];
     const T f[3] = {F[i], F[n + i], F[2 * n + i]};
