@@ -7,16 +7,22 @@ tolerance 1e-6.  One "step" is one npfem_step call advancing every cell by one
 time step (Algorithm 1: first guess, quasi-Newton solve, velocity update,
 post-convergence dissipation).
 
+Chosen form (default): BF16 tensor-core A^-1 contraction with FP32 accumulation and
+FP32 everything else, and the learned warm start, whose network is trained before
+the timed region on trajectories of the plain solver (other cells and seeds).
+
 Legs:
   value     device time of npfem_step with the state resident in HBM (CUDA events on
             the launch stream, L2 flushed between steps because the state fits in L2)
   e2e       the same through npfem_step_host: pinned host buffers copied in and out
             inside the timed region
-  plain     the plain FP32 GPU path (FP32 SIMT contraction, first-guess warm start)
+  plain     the plain FP32 GPU path (FP32 SIMT contraction, first guess y), same
+            cells, steps and residual tolerance
   cpu_baseline / --impl reference
             the FP64 CPU oracle on this machine's cores, on a bounded sample
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--cells C]
+                [--precision bf16|fp32|fp64] [--warmstart learned|none]
 """
 from __future__ import annotations
 
@@ -46,7 +52,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cells", type=int, default=1024)
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="bf16")
+    ap.add_argument("--warmstart", default="learned", choices=["learned", "none"])
+    ap.add_argument("--ws-train-steps", type=int, default=3000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -202,7 +210,7 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------
 # GPU legs
 # ----------------------------------------------------------------------------------
-def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush):
+def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_times=False):
     xs = torch.tensor(W.to_soa(pop["x"][:cells]), dtype=torch.float32, device="cuda")
     vs = torch.tensor(W.to_soa(pop["v"][:cells]), dtype=torch.float32, device="cuda")
     fs = torch.tensor(W.to_soa(pop["f"][:cells]), dtype=torch.float32, device="cuda")
@@ -211,26 +219,29 @@ def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush):
     for _ in range(warmup):
         N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
     torch.cuda.synchronize()
+    if kernel_times:
+        handle.kernel_timing(steps)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    iters = evals = 0
-    statuses = np.zeros(4, dtype=np.int64)
-    res_max = 0.0
+    iters_all = []
+    launches0 = N.launch_count()
     for k in range(steps):
         flush.zero_()  # writes a buffer larger than L2 between timed steps
         ev[k][0].record(stream)
         N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
         ev[k][1].record(stream)
-        if k == steps - 1 or k % 50 == 0:
-            s = st.cpu().numpy().view(N.CELL_STATS_DTYPE).reshape(cells)
     torch.cuda.synchronize()
+    launches = N.launch_count() - launches0
     times = [a.elapsed_time(b) for a, b in ev]
+    ktimes = None
+    if kernel_times:
+        ktimes = handle.kernel_times(steps)
+        handle.kernel_timing(0)
     # statistics of the last step (per-launch work for the roofline)
     s = st.cpu().numpy().view(N.CELL_STATS_DTYPE).reshape(cells)
-    iters, evals = int(s["iterations"].sum()), int(s["evaluations"].sum())
-    for q in range(4):
-        statuses[q] = int((s["status"] == q).sum())
-    res_max = float(s["residual"].max())
-    return times, iters, evals, statuses, res_max
+    statuses = np.array([int((s["status"] == q).sum()) for q in range(4)], dtype=np.int64)
+    return {"times": times, "iters": int(s["iterations"].sum()), "evals": int(s["evaluations"].sum()),
+            "statuses": statuses, "res_max": float(s["residual"].max()), "launches": launches,
+            "kernel_ms": ktimes}
 
 
 def e2e_leg(N, W, handle, pop, cells, steps, warmup, torch):
@@ -252,6 +263,17 @@ def e2e_leg(N, W, handle, pop, cells, steps, warmup, torch):
     return dt, 3 * nb, 2 * nb + 32 * cells
 
 
+def train_warm_start(handle, rank, train_steps):
+    """Trains the warm-start network on trajectories of the plain solver (1000 other
+    cells, 200 steps, seed 100 + rank) and installs it; returns a summary."""
+    from paper_1903_06479_gb300 import learn
+    t0 = time.perf_counter()
+    P, info = learn.train_warmstart(handle, n_cells=1000, steps=200, seed=100 + rank, train_steps=train_steps)
+    handle.set_warmstart(P, 1)
+    return {"train_s": time.perf_counter() - t0, "samples": info["samples"], "step_pairs": info["step_pairs"],
+            "loss_init": info["loss_init"], "loss_final": info["loss_final"], "network": "9-64-64-3 tanh, BF16 operands"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -265,19 +287,23 @@ def main():
     N.lib()
     cells = args.cells
     pop = W.population(N_VERTS, cells, seed=1 + rank, forces="shear", noise_pN=0.5)
-    opts = N.default_opts(precision=args.precision, tol=1e-6, max_iter=50)
+    opts = N.default_opts(precision=args.precision, tol=1e-6, max_iter=50, refine=0)
     handle = N.Handle(pop["rest"], pop["tris"], N.material(), opts, dt=DT, device=local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    ws = None
+    if args.warmstart == "learned" and args.precision != "fp64":
+        ws = train_warm_start(handle, rank, args.ws_train_steps)
 
     barrier(pg)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        times, iters, evals, statuses, res_max = device_leg(N, W, handle, pop, cells, args.steps, args.warmup,
-                                                            torch, flush)
+        dl = device_leg(N, W, handle, pop, cells, args.steps, args.warmup, torch, flush, kernel_times=True)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     barrier(pg)
+    times = dl["times"]
     dev_s = sum(times) / 1e3
     dev_s_max = max_over_ranks(pg, dev_s)
     total_cells = sum_over_ranks(pg, cells)
@@ -285,31 +311,36 @@ def main():
     clocks = clk.summary()
 
     plain = None
-    if not args.no_plain and args.precision != "fp32":
-        hp = N.Handle(pop["rest"], pop["tris"], N.material(), N.default_opts(precision="fp32"), dt=DT, device=local)
-        ksteps = max(10, args.steps // 4)
-        tp, pit, pev, pst, pres = device_leg(N, W, hp, pop, cells, ksteps, 2, torch, flush)
-        plain = {"value": total_cells * ksteps / max_over_ranks(pg, sum(tp) / 1e3), "unit": "RBC-steps/s",
-                 "precision": "fp32", "steps": ksteps, "iterations_per_cell": pit / cells,
-                 "residual_max": pres, "status_counts": pst.tolist()}
+    if not args.no_plain and (args.precision != "fp32" or ws is not None):
+        hp = N.Handle(pop["rest"], pop["tris"], N.material(), N.default_opts(precision="fp32", tol=1e-6, max_iter=50),
+                      dt=DT, device=local)
+        pl = device_leg(N, W, hp, pop, cells, args.steps, args.warmup, torch, flush)
+        plain = {"value": total_cells * args.steps / max_over_ranks(pg, sum(pl["times"]) / 1e3),
+                 "unit": "RBC-steps/s", "form": "FP32 SIMT contraction, first guess y", "steps": args.steps,
+                 "iterations_per_cell": pl["iters"] / cells, "evaluations_per_cell": pl["evals"] / cells,
+                 "residual_max": pl["res_max"], "status_counts": pl["statuses"].tolist()}
         del hp
 
     e2e = None
     if not args.no_e2e:
         barrier(pg)
-        e_s, bi, bo = e2e_leg(N, W, handle, pop, cells, max(5, args.steps // 4), 2, torch)
+        ke = max(5, args.steps // 4)
+        e_s, bi, bo = e2e_leg(N, W, handle, pop, cells, ke, 2, torch)
         e_s = max_over_ranks(pg, e_s)
-        e2e = {"value": total_cells * max(5, args.steps // 4) / e_s, "unit": "RBC-steps/s",
-               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+        e2e = {"value": total_cells * ke / e_s, "unit": "RBC-steps/s", "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "steps": ke}
 
     pk, pk_kind = peaks()
     m = opts.lbfgs_m
-    alg = algorithmic_bytes(N_VERTS, m, iters, evals, cells)
-    t_launch = dev_s / args.steps
-    achieved = alg / t_launch / 1e9
+    alg = algorithmic_bytes(N_VERTS, m, dl["iters"], dl["evals"], cells)
+    kms = dl["kernel_ms"]
+    t_kernel = float(np.mean(kms)) / 1e3 if kms is not None and len(kms) else dev_s / args.steps
+    achieved = alg / t_kernel / 1e9
+    kname = "cell_kernel_tc<float>" if args.precision == "bf16" else "cell_kernel"
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind,
-            "kernel": "cell_kernel<float>", "algorithmic_bytes_per_launch": alg}
+            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "peak_source": f"{pk_kind} (HBM copy bandwidth, MEASURED_PEAKS.json)" if pk_kind == "measured" else pk_kind,
+            "kernel": kname, "kernel_ms_mean": t_kernel * 1e3, "algorithmic_bytes_per_launch": alg}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -320,21 +351,25 @@ def main():
                "sample": f"{sample_cells} cells x 10 time steps of the same workload, FP64, {cores} threads"}
 
     if rank == 0:
+        prec_name = {"bf16": "BF16 tensor-core A^-1 contraction, FP32 elsewhere", "fp32": "FP32",
+                     "fp64": "FP64"}[args.precision]
         line = {"metric": METRIC, "value": value, "unit": "RBC-steps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic",
                 "config": {"workload": f"{cells} RBCs x 642-vertex discocyte per GPU, shear traction U(10,1000)/s "
                                        f"+ N(0,0.5 pN), dt 0.1 us, tol 1e-6",
-                           "cells_per_gpu": cells, "precision": args.precision, "lbfgs_m": m,
+                           "cells_per_gpu": cells, "precision": prec_name,
+                           "warm_start": "learned MLP" if ws is not None else "first guess y", "lbfgs_m": m,
                            "l2": "flushed between timed steps (256 MB write)"},
-                "gpu_launches": args.steps,
+                "gpu_launches": dl["launches"],
                 "wall_s": t_wall,
                 "per_step_ms": {"median": float(np.median(times)), "min": float(np.min(times)),
                                 "max": float(np.max(times))},
-                "solver": {"iterations_per_cell": iters / cells, "evaluations_per_cell": evals / cells,
-                           "status_counts": statuses.tolist(), "residual_max": res_max},
-                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "plain": plain}
+                "solver": {"iterations_per_cell": dl["iters"] / cells, "evaluations_per_cell": dl["evals"] / cells,
+                           "status_counts": dl["statuses"].tolist(), "residual_max": dl["res_max"]},
+                "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "plain": plain,
+                "warm_start": ws}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

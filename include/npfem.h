@@ -262,6 +262,22 @@ int npfem_check_device(npfem_handle* h);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* npfem_last_error(void);
 
+/* Timing of the solver kernels of npfem_step, for measurement: with capacity > 0,
+   the next `capacity` npfem_step calls whose first handle is h record a CUDA event
+   before and after their solver launch(es) (after the warm-start launch) on the
+   call's stream; capacity 0 stops recording and frees the events.  Blocks.
+   Errors: INVALID_ARG, CUDA. */
+int npfem_kernel_timing(npfem_handle* h, int capacity);
+
+/* Durations in ms of the recorded solver launches (oldest first) into ms_out (up to
+   max entries, *count set to the number written); synchronises on the events and
+   restarts the recording.  Errors: INVALID_ARG, CUDA. */
+int npfem_kernel_times(npfem_handle* h, float* ms_out, int max, int* count);
+
+/* Number of kernels the library has launched in this process (all devices, all
+   entry points), for counting device work; thread-safe, never fails. */
+unsigned long long npfem_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

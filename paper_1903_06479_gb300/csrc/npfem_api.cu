@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -28,6 +29,11 @@ int fail(int code, const std::string& msg)
 }  // namespace
 
 int npfem::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+namespace npfem {
+std::atomic<unsigned long long> g_launches{0};
+void count_launch(unsigned long long k) { g_launches.fetch_add(k); }
+}  // namespace npfem
 
 namespace {
 
@@ -341,6 +347,34 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     return 0;
 }
 
+// The solver launches of one step (tensor-core kernel per group when every group fits
+// it in BF16, else one SIMT launch over all groups).
+int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
+                const void* f_ext, cudaStream_t s, npfem_cell_stats* stats, const float* u0)
+{
+    if (meshes[0]->precision == NPFEM_PREC_BF16) {
+        bool all_tc = true;
+        for (int g = 0; g < n_groups; ++g) all_tc = all_tc && meshes[g]->n <= kTcMaxVerts;
+        if (all_tc) {
+            long long cell0 = 0, state0 = 0;
+            for (int g = 0; g < n_groups; ++g) {
+                int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + state0, (float*)v + state0,
+                                      (const float*)f_ext + state0, stats ? stats + cell0 : nullptr, s,
+                                      u0 ? u0 + state0 : nullptr);
+                if (rc) return rc;
+                cell0 += cells_per_group[g];
+                state0 += 3LL * meshes[g]->n * cells_per_group[g];
+            }
+            return 0;
+        }
+    }
+    if (meshes[0]->precision == NPFEM_PREC_FP64)
+        return run_cells<double>(meshes, n_groups, cells_per_group, (double*)x, (double*)v, (const double*)f_ext,
+                                 nullptr, nullptr, nullptr, stats, 0, s);
+    return run_cells<float>(meshes, n_groups, cells_per_group, (float*)x, (float*)v, (const float*)f_ext, nullptr,
+                            nullptr, nullptr, stats, 0, s, u0);
+}
+
 // Learned first increments of every group with a warm start, into meshes[0]'s
 // buffer at the groups' state offsets (a separate launch: in the cluster kernel a
 // block computing them would hold up its whole cluster).  Null when no group has one.
@@ -411,6 +445,40 @@ void npfem_default_opts(npfem_opts* o)
 }
 
 const char* npfem_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long npfem_launch_count(void) { return npfem::g_launches.load(); }
+
+int npfem_kernel_timing(npfem_handle* h, int capacity)
+{
+    if (!h || capacity < 0) return fail(NPFEM_ERR_INVALID_ARG, "npfem_kernel_timing: bad argument");
+    DeviceGuard guard(h->device);
+    std::lock_guard<std::mutex> lk(h->mu);
+    NPFEM_CUDA(cudaDeviceSynchronize());
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+    h->tev.clear();
+    h->tev_used = 0;
+    for (int q = 0; q < 2 * capacity; ++q) {
+        cudaEvent_t e;
+        NPFEM_CUDA(cudaEventCreate(&e));
+        h->tev.push_back(e);
+    }
+    return 0;
+}
+
+int npfem_kernel_times(npfem_handle* h, float* ms_out, int max, int* count)
+{
+    if (!h || !count || max < 0 || (max > 0 && !ms_out)) return fail(NPFEM_ERR_INVALID_ARG, "npfem_kernel_times: bad argument");
+    DeviceGuard guard(h->device);
+    std::lock_guard<std::mutex> lk(h->mu);
+    int k = 0;
+    for (int q = 0; q + 1 < h->tev_used && k < max; q += 2, ++k) {
+        NPFEM_CUDA(cudaEventSynchronize(h->tev[q + 1]));
+        NPFEM_CUDA(cudaEventElapsedTime(&ms_out[k], h->tev[q], h->tev[q + 1]));
+    }
+    *count = k;
+    h->tev_used = 0;
+    return 0;
+}
 
 int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_opts* opts, double dt, int device,
                  npfem_handle** out)
@@ -543,27 +611,15 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
                                            (const float*)f_ext, s, &u0))
             return rc;
     }
-    if (meshes[0]->precision == NPFEM_PREC_BF16) {
-        bool all_tc = true;
-        for (int g = 0; g < n_groups; ++g) all_tc = all_tc && meshes[g]->n <= kTcMaxVerts;
-        if (all_tc) {
-            long long cell0 = 0, state0 = 0;
-            for (int g = 0; g < n_groups; ++g) {
-                int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + state0, (float*)v + state0,
-                                      (const float*)f_ext + state0, stats ? stats + cell0 : nullptr, s,
-                                      u0 ? u0 + state0 : nullptr);
-                if (rc) return rc;
-                cell0 += cells_per_group[g];
-                state0 += 3LL * meshes[g]->n * cells_per_group[g];
-            }
-            return 0;
-        }
+    npfem_handle* h0 = meshes[0];
+    const bool timed = h0->tev_used + 2 <= (int)h0->tev.size();
+    if (timed) NPFEM_CUDA(cudaEventRecord(h0->tev[h0->tev_used], s));
+    int rc = step_groups(meshes, n_groups, cells_per_group, x, v, f_ext, s, stats, u0);
+    if (!rc && timed) {
+        NPFEM_CUDA(cudaEventRecord(h0->tev[h0->tev_used + 1], s));
+        h0->tev_used += 2;
     }
-    if (meshes[0]->precision == NPFEM_PREC_FP64)
-        return run_cells<double>(meshes, n_groups, cells_per_group, (double*)x, (double*)v, (const double*)f_ext,
-                                 nullptr, nullptr, nullptr, stats, 0, s);
-    return run_cells<float>(meshes, n_groups, cells_per_group, (float*)x, (float*)v, (const float*)f_ext, nullptr,
-                            nullptr, nullptr, stats, 0, s, u0);
+    return rc;
 }
 
 int npfem_step_host(npfem_handle* h, int n_cells, void* x_host, void* v_host, const void* f_host, double dt,

@@ -91,6 +91,7 @@ __global__ void publish_bf16_blocked(const double* A, int n, int rows_pad, int k
 cudaError_t publish_inverse_bf16_blocked(const double* A, int n, int rows_pad, int kpad, void* out, cudaStream_t s)
 {
     publish_bf16_blocked<<<1024, 256, 0, s>>>(A, n, rows_pad, kpad, (__nv_bfloat16*)out);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -100,6 +101,7 @@ cudaError_t invert_spd_fp64(double* A, int n, double* col, int* d_flag, cudaStre
     for (int k = 0; k < n; ++k) {
         gj_pivot_row<<<1, 512, 0, s>>>(A, col, n, k, d_flag);
         gj_update<<<ug, ub, 0, s>>>(A, col, n, k);
+        count_launch(2);
     }
     return cudaGetLastError();
 }
@@ -108,7 +110,9 @@ cudaError_t publish_inverse(const double* A, int n, int n_pad, float* o32, doubl
                             cudaStream_t s)
 {
     symmetrise_inplace<<<1024, 256, 0, s>>>(const_cast<double*>(A), n);
+    count_launch();
     symmetrise_publish<<<1024, 256, 0, s>>>(A, n, n_pad, o32, o64, (__nv_bfloat16*)obf, otf);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -179,6 +179,9 @@ constexpr int kTcMaxVerts = 960;
 // Records msg as the calling thread's last error and returns code (npfem_api.cu).
 int set_error(int code, const std::string& msg);
 
+// Counts a kernel launch of the library (npfem_launch_count).
+void count_launch(unsigned long long k = 1);
+
 // Places the per-cell buffers: shared memory in priority order while they fit (the
 // randomly gathered ones first; GC first of all with gc_first), the rest in a
 // per-block global slot.  smem offsets
@@ -256,6 +259,9 @@ struct npfem_handle {
     void* hf = nullptr;
     npfem_cell_stats* hstats = nullptr;
     size_t host_cells = 0;
+    // optional timing of the solver kernel launches of npfem_step (event pairs)
+    std::vector<cudaEvent_t> tev;
+    int tev_used = 0;
     std::mutex mu;
 
     template <typename X>
@@ -287,5 +293,8 @@ struct npfem_handle {
         if (hstats) cudaFree(hstats);
         hx = hv = hf = nullptr;
         hstats = nullptr;
+        for (cudaEvent_t e : tev) cudaEventDestroy(e);
+        tev.clear();
+        tev_used = 0;
     }
 };

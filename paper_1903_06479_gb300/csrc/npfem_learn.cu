@@ -328,6 +328,7 @@ cudaError_t launch_ws_increments(const npfem_handle* h, int n_cells, const float
     const int per_sm = smem <= h->smem_optin / 2 ? 2 : 1;
     const int grid = std::min(n_cells, per_sm * h->sm_count);
     ws_increment_kernel<<<grid, 512, smem, s>>>(h->tf, n_cells, x, v, f, out, positions ? 1 : 0);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -355,6 +356,7 @@ int npfem_mlp_loss_grad(const float* params, const float* feat, const float* tar
     const int tiles = (n + kTile - 1) / kTile;
     const int grid = std::max(1, std::min(tiles, 2 * sms));
     mlp_grad_kernel<<<grid, 256, kGradSmem, s>>>(params, feat, target, idx, n, 1.f / n, grad, loss);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_mlp_loss_grad: ") + cudaGetErrorString(e));
     return 0;
@@ -365,6 +367,7 @@ int npfem_mlp_adam(float* params, float* m, float* v, const float* grad, int ste
 {
     if (!params || !m || !v || !grad || step < 1) return set_error(NPFEM_ERR_INVALID_ARG, "npfem_mlp_adam: bad argument");
     mlp_adam_kernel<<<20, 256, 0, static_cast<cudaStream_t>(stream)>>>(params, m, v, grad, step, lr, beta1, beta2, eps);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_mlp_adam: ") + cudaGetErrorString(e));
     return 0;
@@ -376,6 +379,7 @@ int npfem_mlp_predict(const float* params, const float* feat, int n, float* out,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     mlp_round_kernel<<<20, 256, 0, s>>>(params, scratch);
     if (n > 0) mlp_predict_kernel<<<std::max(1, std::min((n + 63) / 64, 4096)), 128, 0, s>>>(scratch, feat, n, out);
+    count_launch(n > 0 ? 2 : 1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_mlp_predict: ") + cudaGetErrorString(e));
     return 0;
@@ -394,6 +398,7 @@ int npfem_ws_features(npfem_handle* h, int n_cells, const float* x, const float*
     cudaError_t e = cudaFuncSetAttribute(ws_features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_ws_features: ") + cudaGetErrorString(e));
     ws_features_kernel<<<std::min(n_cells, 4 * h->sm_count), 256, smem, s>>>(h->tf, n_cells, x, v, f, x_next, feat, target);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_ws_features: ") + cudaGetErrorString(e));
     return 0;

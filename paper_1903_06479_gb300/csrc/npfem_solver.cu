@@ -1491,6 +1491,7 @@ template <typename T>
 cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s)
 {
     cell_kernel<T><<<grid, block, smem, s>>>(a);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -1528,6 +1529,7 @@ cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, 
     *grid_out = (int)(want * cluster);
     e = wide ? cudaLaunchKernelEx(&cfg, kern32, a) : cudaLaunchKernelEx(&cfg, kern16, a);
     if (e != cudaSuccess) return e;
+    count_launch();
     return cudaGetLastError();
 }
 

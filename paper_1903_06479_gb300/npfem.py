@@ -49,7 +49,8 @@ _lib = None
 EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", "npfem_step_host", "npfem_eval",
            "npfem_get_inverse", "npfem_get_rest_info", "npfem_last_error", "npfem_step_static",
            "npfem_check_device", "npfem_mlp_nparam", "npfem_ws_features", "npfem_mlp_loss_grad", "npfem_mlp_adam",
-           "npfem_mlp_predict", "npfem_set_warmstart", "npfem_ws_guess")
+           "npfem_mlp_predict", "npfem_set_warmstart", "npfem_ws_guess", "npfem_launch_count",
+           "npfem_kernel_timing", "npfem_kernel_times")
 
 
 def lib_path() -> str:
@@ -63,6 +64,10 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         vp, i32 = C.c_void_p, C.c_int
+        L.npfem_kernel_timing.argtypes = [vp, i32]
+        L.npfem_kernel_times.argtypes = [vp, vp, i32, vp]
+        L.npfem_launch_count.argtypes = []
+        L.npfem_launch_count.restype = C.c_ulonglong
         L.npfem_default_opts.argtypes = [C.POINTER(Opts)]
         L.npfem_default_opts.restype = None
         L.npfem_create.argtypes = [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Opts), C.c_double, i32, C.POINTER(vp)]
@@ -189,6 +194,17 @@ class Handle:
         _check(lib().npfem_get_rest_info(self._h, m.ctypes.data, s.ctypes.data))
         return m, dict(V0=s[0], A0=s[1], lbar=s[2], mtotal=s[3])
 
+    def kernel_timing(self, capacity: int):
+        """Record the solver-kernel time of the next `capacity` steps (0: stop)."""
+        _check(lib().npfem_kernel_timing(self._h, int(capacity)))
+
+    def kernel_times(self, max_n: int = 4096) -> np.ndarray:
+        """Durations (ms) of the recorded solver launches; restarts the recording."""
+        out = np.zeros(max_n, dtype=np.float32)
+        n = C.c_int(0)
+        _check(lib().npfem_kernel_times(self._h, out.ctypes.data, int(max_n), C.addressof(n)))
+        return out[:n.value].copy()
+
     def eval(self, n_cells: int, x, y, grad, parts, stream=None):
         _check(lib().npfem_eval(self._h, n_cells, _addr(x), _addr(y), _addr(grad), _addr(parts), _addr(stream)))
 
@@ -215,6 +231,11 @@ def step_static(handles, cells_per_group, x, v, f, dt: float, stream=None, stats
     cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
     _check(lib().npfem_step_static(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), _addr(stream),
                                    _addr(stats)))
+
+
+def launch_count() -> int:
+    """Kernels the library has launched so far in this process."""
+    return int(lib().npfem_launch_count())
 
 
 def mlp_nparam() -> int:
