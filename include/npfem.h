@@ -99,7 +99,9 @@ typedef struct {
    armijo_noise: multiple of the estimated rounding error of g added to the
                  Armijo bound (FP32 energies); 0 = exact test.
    refine: NPFEM_PREC_BF16 only: refinement sweeps of the tensor-core A^-1
-           contraction (0 or 1): r = A^-1 q, then r += A^-1 (q - H~ r). */
+           contraction (0 or 1): r = A^-1 q, then r += A^-1 (q - H~ r).
+   fill_idle_sms: NPFEM_PREC_BF16 only: 1 = SMs that the tensor-core clusters leave
+           idle run the SIMT solver on the same cells (dynamic split), 0 = clusters only. */
 typedef struct {
     int32_t precision;
     int32_t lbfgs_m;
@@ -111,6 +113,7 @@ typedef struct {
     int32_t equal_mass;
     double armijo_noise;
     int32_t refine;
+    int32_t fill_idle_sms;
 } npfem_opts;
 
 /* Per-cell result of one npfem_step call (device memory, 32 bytes). */

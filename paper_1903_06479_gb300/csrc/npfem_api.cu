@@ -218,6 +218,8 @@ int check_opts(const npfem_opts* o)
         !(o->armijo_noise >= 0.0))
         return fail(NPFEM_ERR_INVALID_ARG, "opts: need tol >= 0, 0 < c1 < c2 < 1, armijo_noise >= 0");
     if (o->refine < 0 || o->refine > 1) return fail(NPFEM_ERR_INVALID_ARG, "opts.refine must be 0 or 1");
+    if (o->fill_idle_sms < 0 || o->fill_idle_sms > 1)
+        return fail(NPFEM_ERR_INVALID_ARG, "opts.fill_idle_sms must be 0 or 1");
     if (o->precision == NPFEM_PREC_TF32)
         return fail(NPFEM_ERR_INVALID_ARG,
                     "NPFEM_PREC_TF32 is not available: a TF32 row block of A^-1 does not fit in tensor memory; "
@@ -326,10 +328,31 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     // allocation while its cluster waits for it
     int smem = kFixedSmem + g.smem_bytes;
     smem = std::max(smem, h->smem_optin / 2 + 4096);
+    int max_clusters = 0;
+    NPFEM_CUDA(query_cells_tc(cluster, h->threads, smem, &max_clusters));
+    const long long want = std::min<long long>((cells + cluster - 1) / cluster, max_clusters);
+    const int grid = (int)(want * cluster);
+
+    // SMs the clusters leave idle (clusters stay within a GPC) run the SIMT kernel on
+    // the same work counter: each cell goes to whichever kind of block asks first
+    LaunchArgs<float> b;
+    long long slot_b = 0;
+    int smem_b = 0;
+    int helper = h->sm_count - grid;
+    if (cells <= grid || h->opts.fill_idle_sms == 0) helper = 0;
+    if (helper > 0) {
+        b = a;
+        place_vectors(&b.g[0], h->n_pad, h->nt, h->opts.lbfgs_m, h->smem_optin - kFixedSmem - 1024, &slot_b);
+        b.p.contraction = CONTRACT_SIMT;
+        b.p.cluster = 0;
+        b.p.refine = 0;
+        smem_b = kFixedSmem + b.g[0].smem_bytes;
+        if (smem_b <= h->smem_optin / 2) helper = 0;  // would share SMs with the clusters
+    }
+    a.total_blocks = grid + helper;
     a.slot_bytes = slot;
-    const long long max_grid = (long long)h->sm_count;
-    if (slot > 0) {
-        size_t need = (size_t)slot * (size_t)max_grid;
+    const size_t need = (size_t)slot * (size_t)grid + (size_t)slot_b * (size_t)helper;
+    if (need > 0) {
         if (need > h->scratch_bytes) {
             if (h->scratch) {
                 NPFEM_CUDA(cudaStreamSynchronize(stream));
@@ -340,10 +363,36 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
             NPFEM_CUDA(cudaMalloc(&h->scratch, need));
             h->scratch_bytes = need;
         }
-        a.scratch = h->scratch;
+        a.scratch = slot > 0 ? h->scratch : nullptr;
     }
-    int grid = 0;
-    NPFEM_CUDA(launch_cells_tc(a, cluster, h->threads, smem, stream, &grid));
+    if (helper > 0) {
+        b.total_blocks = a.total_blocks;
+        b.claim_top = 1;
+        b.reserve = grid;  // about one cell per cluster block: the helper's cells take longer
+        b.slot_bytes = slot_b;
+        b.scratch = slot_b > 0 ? h->scratch + (size_t)slot * (size_t)grid : nullptr;
+        if (!h->side_stream) {
+            NPFEM_CUDA(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+            NPFEM_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+            NPFEM_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        }
+        NPFEM_CUDA(cudaEventRecord(h->ev_fork, stream));
+    }
+    NPFEM_CUDA(launch_cells_tc(a, cluster, h->threads, smem, grid, stream));
+    if (helper > 0) {
+        cudaError_t e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
+        if (e == cudaSuccess) e = set_cell_kernel_smem<float>(smem_b);
+        if (e == cudaSuccess) e = launch_cells<float>(b, helper, h->threads, smem_b, h->side_stream);
+        if (e != cudaSuccess) {
+            // the clusters alone cannot reset the shared counters: clear them behind
+            // the launch so that the next step starts clean, and report the failure
+            cudaMemsetAsync(h->work, 0, 2 * sizeof(unsigned), stream);
+            cudaMemsetAsync(h->work + 3, 0, sizeof(unsigned), stream);
+            return fail(NPFEM_ERR_CUDA, std::string("idle-SM launch: ") + cudaGetErrorString(e));
+        }
+        NPFEM_CUDA(cudaEventRecord(h->ev_join, h->side_stream));
+        NPFEM_CUDA(cudaStreamWaitEvent(stream, h->ev_join, 0));
+    }
     return 0;
 }
 
@@ -441,7 +490,8 @@ void npfem_default_opts(npfem_opts* o)
     o->fixed_alpha = 0;
     o->equal_mass = 0;
     o->armijo_noise = 4.0;
-    o->refine = 1;
+    o->refine = 0;
+    o->fill_idle_sms = 1;
 }
 
 const char* npfem_last_error(void) { return g_last_error.c_str(); }

@@ -125,7 +125,12 @@ struct LaunchArgs {
     npfem_cell_stats* stats;
     char* scratch;     // per-CTA global slots for vectors that do not fit in smem
     long long slot_bytes;
-    unsigned int* work;  // [0] next work item, [1] finished blocks (reset by the last block), [2] error flag
+    // [0..1] 64-bit claim word (low half: cells claimed from the bottom, high half: from
+    // the top), [2] error flag, [3] finished blocks; the last block resets [0..1] and [3]
+    unsigned int* work;
+    int total_blocks;    // blocks of all launches sharing `work` (0: this launch's grid)
+    int claim_top;       // 1: claim cells from the top and stop while at most `reserve` remain
+    long long reserve;
     SolverParams p;
 };
 
@@ -164,10 +169,11 @@ template <typename T>
 cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s);
 template <typename T>
 cudaError_t set_cell_kernel_smem(int bytes);
-// Tensor-core (BF16, A^-1 row blocks resident in TMEM across a cluster) launch of one
-// mesh group; sets *grid_out.
-cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, int smem, cudaStream_t s,
-                            int* grid_out);
+// Tensor-core kernel (BF16, A^-1 row blocks resident in TMEM across a cluster): sets
+// its shared-memory size and returns how many clusters can be resident at once.
+cudaError_t query_cells_tc(int cluster, int block, int smem, int* max_clusters);
+// Launch of one mesh group on `grid` blocks (a multiple of the cluster size).
+cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, int smem, int grid, cudaStream_t s);
 // Learned first increments u = x^(1) - x_n ([3][n] per cell, or positions x_n + u
 // when positions is set) of n_cells cells of handle h (npfem_learn.cu).
 cudaError_t launch_ws_increments(const npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
@@ -259,6 +265,9 @@ struct npfem_handle {
     void* hf = nullptr;
     npfem_cell_stats* hstats = nullptr;
     size_t host_cells = 0;
+    // side stream and fork/join events of the idle-SM SIMT launch (tensor-core path)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // optional timing of the solver kernel launches of npfem_step (event pairs)
     std::vector<cudaEvent_t> tev;
     int tev_used = 0;
@@ -296,5 +305,10 @@ struct npfem_handle {
         for (cudaEvent_t e : tev) cudaEventDestroy(e);
         tev.clear();
         tev_used = 0;
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side_stream) cudaStreamDestroy(side_stream);
+        ev_fork = ev_join = nullptr;
+        side_stream = nullptr;
     }
 };

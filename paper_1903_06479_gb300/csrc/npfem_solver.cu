@@ -1092,22 +1092,42 @@ template <typename T>
 __device__ __forceinline__ long long next_item(const LaunchArgs<T>& a, unsigned char* smem)
 {
     CellShared<T>* sh = cell_shared<T>(smem);
-    if (threadIdx.x == 0) sh->item = (long long)atomicAdd(&a.work[0], 1u);
+    if (threadIdx.x == 0) {
+        unsigned long long* cw = reinterpret_cast<unsigned long long*>(a.work);
+        long long item = -1;
+        if (a.claim_top) {
+            // a slower helper: leaves the last `reserve` cells to the main launch
+            const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(cw);
+            const long long left = a.total_cells - (long long)(cur & 0xffffffffull) - (long long)(cur >> 32);
+            if (left > a.reserve) {
+                const unsigned long long old = atomicAdd(cw, 1ull << 32);
+                const long long lo = (long long)(old & 0xffffffffull), hi = (long long)(old >> 32);
+                if (lo + hi < a.total_cells) item = a.total_cells - 1 - hi;
+            }
+        } else {
+            const unsigned long long old = atomicAdd(cw, 1ull);
+            const long long lo = (long long)(old & 0xffffffffull), hi = (long long)(old >> 32);
+            if (lo + hi < a.total_cells) item = lo;
+        }
+        sh->item = item;
+    }
     __syncthreads();
     const long long it = sh->item;
     __syncthreads();
-    return it < a.total_cells ? it : -1;
+    return it;
 }
 
-// The last block to finish resets the work counters for the next launch.
-__device__ __forceinline__ void release_counters(unsigned int* work)
+// The last block to finish (of all launches sharing the counters) resets them for the
+// next launch.
+__device__ __forceinline__ void release_counters(unsigned int* work, int total_blocks)
 {
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned prev = atomicAdd(&work[1], 1u);
-        if (prev == gridDim.x * gridDim.y * gridDim.z - 1) {
-            atomicExch(&work[0], 0u);
-            atomicExch(&work[1], 0u);
+        const unsigned prev = atomicAdd(&work[3], 1u);
+        const unsigned total = total_blocks > 0 ? (unsigned)total_blocks : gridDim.x * gridDim.y * gridDim.z;
+        if (prev == total - 1) {
+            atomicExch(reinterpret_cast<unsigned long long*>(work), 0ull);
+            atomicExch(&work[3], 0u);
         }
     }
 }
@@ -1139,7 +1159,7 @@ __global__ void __launch_bounds__(512, 1) cell_kernel(const __grid_constant__ La
         }
         S.finish();
     }
-    release_counters(a.work);
+    release_counters(a.work, a.total_blocks);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1476,7 +1496,7 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     tc::cluster_sync();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
-    release_counters(a.work);
+    release_counters(a.work, a.total_blocks);
 }
 
 }  // namespace
@@ -1495,39 +1515,48 @@ cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, 
     return cudaGetLastError();
 }
 
-// Cluster launch of the tensor-core kernel for one mesh group; returns the grid in
-// *grid_out (cluster size x co-resident clusters, capped by the cell count).
-cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, int smem, cudaStream_t s,
-                            int* grid_out)
+static cudaLaunchConfig_t tc_config(int cluster, int block, int smem, int grid, cudaStream_t s, cudaLaunchAttribute* attr)
 {
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(block);
+    cfg.gridDim = dim3(grid);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cfg;
+}
+
+cudaError_t query_cells_tc(int cluster, int block, int smem, int* max_clusters)
+{
     const bool wide = cluster * 3 > 16;
     auto kern32 = cell_kernel_tc<float, 32>;
     auto kern16 = cell_kernel_tc<float, 16>;
     cudaError_t e = wide ? cudaFuncSetAttribute(kern32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
                          : cudaFuncSetAttribute(kern16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    int nclusters = 0;
-    cfg.gridDim = dim3(cluster);
-    e = wide ? cudaOccupancyMaxActiveClusters(&nclusters, kern32, &cfg)
-             : cudaOccupancyMaxActiveClusters(&nclusters, kern16, &cfg);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tc_config(cluster, block, smem, cluster, nullptr, attr);
+    int n = 0;
+    e = wide ? cudaOccupancyMaxActiveClusters(&n, kern32, &cfg) : cudaOccupancyMaxActiveClusters(&n, kern16, &cfg);
     if (e != cudaSuccess) return e;
-    if (nclusters < 1) return cudaErrorInvalidConfiguration;
-    long long want = (a.total_cells + cluster - 1) / cluster;
-    if (want > nclusters) want = nclusters;
-    cfg.gridDim = dim3((unsigned)(want * cluster));
-    *grid_out = (int)(want * cluster);
-    e = wide ? cudaLaunchKernelEx(&cfg, kern32, a) : cudaLaunchKernelEx(&cfg, kern16, a);
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    *max_clusters = n;
+    return cudaSuccess;
+}
+
+// Cluster launch of the tensor-core kernel for one mesh group.
+cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, int smem, int grid, cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tc_config(cluster, block, smem, grid, s, attr);
+    const bool wide = cluster * 3 > 16;
+    cudaError_t e = wide ? cudaLaunchKernelEx(&cfg, cell_kernel_tc<float, 32>, a)
+                         : cudaLaunchKernelEx(&cfg, cell_kernel_tc<float, 16>, a);
     if (e != cudaSuccess) return e;
     count_launch();
     return cudaGetLastError();

@@ -289,3 +289,51 @@ def test_tf32_is_rejected(npfem):
     with pytest.raises(npfem.NpfemError) as e:
         make_handle(npfem, 258, "tf32")
     assert e.value.code == -1
+
+
+def _volumes(x, tris):
+    a, b, c = x[:, tris[:, 0]], x[:, tris[:, 1]], x[:, tris[:, 2]]
+    return np.einsum("cti,cti->ct", a, np.cross(b, c)).sum(1) / 6.0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_multistep_drift_against_fp64_oracle(npfem, prec):
+    """20 steps of 8 cells under N(0, 2 pN) noise plus 1000/s shear: positions and
+    volumes against the FP64 oracle (run to 1e-10).  Each step converges to 1e-6 and
+    carries at most the one-step bound 1e-5 l̄ (FP32 and BF16 alike); errors of
+    successive steps add at most linearly, so 20 steps stay within 2e-4 l̄, and the
+    relative volume error within 3 * 2e-4 l̄ / R (R the cell's mean radius)."""
+    steps = 20
+    h = make_handle(npfem, 642, prec, tol=1e-6)
+    m, rest, tris = oracle_model(642)
+    p = population32(642, 8, seed=60, forces="shear", gamma_fixed=1000.0, noise_pN=2.0)
+    xo, vo, _ = oracle_steps(m, p["x"], p["v"], p["f"], steps=steps, tol=1e-10, max_iter=200)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"], steps=steps)
+    assert (sg["status"] == 0).all()
+    drift = max_rel_disp(xg, xo, m.lbar)
+    assert drift <= steps * 1e-5 + fp32_store_allowance(p["x"], m.lbar)
+    R = np.linalg.norm(rest - rest.mean(0), axis=1).mean()
+    verr = np.abs(_volumes(xg, tris) / _volumes(xo, tris) - 1.0).max()
+    assert verr <= 3 * steps * 1e-5 * m.lbar / R
+
+
+def test_bf16_idle_sm_fill_matches_clusters_only(npfem):
+    """With more cells than cluster blocks, SMs the clusters leave idle solve cells with
+    the SIMT kernel from the same work counter; every cell converges either way and the
+    two splits agree to the solver tolerance (and both to the oracle on a sample)."""
+    cells = 400
+    m, _, _ = oracle_model(642)
+    p = population32(642, cells, seed=70, forces="shear", noise_pN=0.5)
+    out = {}
+    for fill in (0, 1):
+        h = make_handle(npfem, 642, "bf16", tol=1e-6, fill_idle_sms=fill)
+        n0 = npfem.launch_count()
+        xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"], steps=2)
+        out[fill] = (xg, npfem.launch_count() - n0)
+        h.check_device()
+        assert (sg["status"] == 0).all() and (sg["residual"] <= 1e-6).all()
+    assert max_rel_disp(out[0][0], out[1][0], m.lbar) <= 2e-5
+    assert out[0][1] == 2 and out[1][1] >= 2  # clusters only: one launch per step
+    sample = [0, 137, 399]
+    xo, _, _ = oracle_steps(m, p["x"][sample], p["v"][sample], p["f"][sample], steps=2, tol=1e-10, max_iter=200)
+    assert max_rel_disp(out[1][0][sample], xo, m.lbar) <= 2e-5 + fp32_store_allowance(p["x"], m.lbar)
