@@ -145,8 +145,12 @@ int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_
 /* Releases the handle and its device memory (synchronises its device). */
 int npfem_destroy(npfem_handle* h);
 
-/* Advances every cell of n_groups meshes by one time step (Algorithm 1), in one
-   kernel launch on `stream` (a cudaStream_t; 0 = legacy default stream).
+/* Advances every cell of n_groups meshes by one time step (Algorithm 1) on `stream`
+   (a cudaStream_t; 0 = legacy default stream): one persistent solver launch over all
+   groups (NPFEM_PREC_BF16 with every mesh of at most 960 vertices: one cluster launch
+   per group, plus a SIMT launch on SMs the clusters leave idle, forked from and
+   joined back to `stream`), preceded by the warm-start launch when a network is
+   installed.
    meshes[g] and cells_per_group[g] (host arrays) name each group; all handles must
    share device, precision and dt.
    x, v: device SoA state (float, or double for NPFEM_PREC_FP64), updated in place
@@ -264,6 +268,21 @@ int npfem_check_device(npfem_handle* h);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* npfem_last_error(void);
+
+/* A CUDA graph of `steps` consecutive npfem_step calls on fixed state buffers (the
+   batching pattern of a time loop: the whole step, warm start and solver launches
+   included, replays as one graph launch).  Creation runs one step on temporary copies
+   of x and v (sizing the handles' buffers; x, v are not modified, stats is written)
+   and captures the steps on an internal stream.  The graph holds the pointers it was
+   created with; it must be destroyed before the handles.  Errors: INVALID_ARG, CUDA,
+   OOM. */
+typedef struct npfem_graph npfem_graph;
+int npfem_graph_create(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
+                       const void* f_ext, double dt, int steps, npfem_cell_stats* stats, npfem_graph** out);
+/* Enqueues the graph's steps on `stream` (asynchronous; npfem_launch_count grows by
+   the kernels of the captured steps).  Errors: INVALID_ARG, CUDA. */
+int npfem_graph_launch(npfem_graph* g, void* stream);
+int npfem_graph_destroy(npfem_graph* g);
 
 /* Timing of the solver kernels of npfem_step, for measurement: with capacity > 0,
    the next `capacity` npfem_step calls whose first handle is h record a CUDA event

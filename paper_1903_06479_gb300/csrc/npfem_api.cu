@@ -328,8 +328,11 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     // allocation while its cluster waits for it
     int smem = kFixedSmem + g.smem_bytes;
     smem = std::max(smem, h->smem_optin / 2 + 4096);
-    int max_clusters = 0;
-    NPFEM_CUDA(query_cells_tc(cluster, h->threads, smem, &max_clusters));
+    if (h->tc_smem != smem) {
+        NPFEM_CUDA(query_cells_tc(cluster, h->threads, smem, &h->tc_max_clusters));
+        h->tc_smem = smem;
+    }
+    const int max_clusters = h->tc_max_clusters;
     const long long want = std::min<long long>((cells + cluster - 1) / cluster, max_clusters);
     const int grid = (int)(want * cluster);
 

@@ -265,6 +265,8 @@ struct npfem_handle {
     void* hf = nullptr;
     npfem_cell_stats* hstats = nullptr;
     size_t host_cells = 0;
+    // resident clusters of the tensor-core kernel at tc_smem bytes (queried once)
+    int tc_max_clusters = 0, tc_smem = -1;
     // side stream and fork/join events of the idle-SM SIMT launch (tensor-core path)
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

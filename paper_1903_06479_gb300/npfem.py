@@ -51,7 +51,8 @@ EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", 
            "npfem_get_inverse", "npfem_get_rest_info", "npfem_last_error", "npfem_step_static",
            "npfem_check_device", "npfem_mlp_nparam", "npfem_ws_features", "npfem_mlp_loss_grad", "npfem_mlp_adam",
            "npfem_mlp_predict", "npfem_set_warmstart", "npfem_ws_guess", "npfem_launch_count",
-           "npfem_kernel_timing", "npfem_kernel_times")
+           "npfem_kernel_timing", "npfem_kernel_times", "npfem_graph_create", "npfem_graph_launch",
+           "npfem_graph_destroy")
 
 
 def lib_path() -> str:
@@ -65,6 +66,9 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         vp, i32 = C.c_void_p, C.c_int
+        L.npfem_graph_create.argtypes = [vp, i32, vp, vp, vp, vp, C.c_double, i32, vp, C.POINTER(vp)]
+        L.npfem_graph_launch.argtypes = [vp, vp]
+        L.npfem_graph_destroy.argtypes = [vp]
         L.npfem_kernel_timing.argtypes = [vp, i32]
         L.npfem_kernel_times.argtypes = [vp, vp, i32, vp]
         L.npfem_launch_count.argtypes = []
@@ -223,6 +227,35 @@ def step(handles, cells_per_group, x, v, f, dt: float, stream=None, stats=None):
     cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
     _check(lib().npfem_step(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), _addr(stream),
                             _addr(stats)))
+
+
+class StepGraph:
+    """npfem_graph_*: `steps` consecutive npfem_step calls on fixed buffers captured as
+    one CUDA graph; launch() replays them on a stream.  Keep the handles alive."""
+
+    def __init__(self, handles, cells_per_group, x, v, f, dt: float, steps: int = 1, stats=None):
+        handles = list(handles)
+        self._handles = handles
+        arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+        cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
+        self._g = C.c_void_p()
+        _check(lib().npfem_graph_create(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), int(steps),
+                                        _addr(stats), C.byref(self._g)))
+        self.steps = steps
+
+    def launch(self, stream=None):
+        _check(lib().npfem_graph_launch(self._g, _addr(stream)))
+
+    def close(self):
+        if self._g:
+            lib().npfem_graph_destroy(self._g)
+            self._g = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def step_static(handles, cells_per_group, x, v, f, dt: float, stream=None, stats=None):

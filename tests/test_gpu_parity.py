@@ -337,3 +337,46 @@ def test_bf16_idle_sm_fill_matches_clusters_only(npfem):
     sample = [0, 137, 399]
     xo, _, _ = oracle_steps(m, p["x"][sample], p["v"][sample], p["f"][sample], steps=2, tol=1e-10, max_iter=200)
     assert max_rel_disp(out[1][0][sample], xo, m.lbar) <= 2e-5 + fp32_store_allowance(p["x"], m.lbar)
+
+
+def test_single_cell_fp64_ten_steps(npfem):
+    """One 258-vertex discocyte, FP64 on the GPU, i.i.d. N(0, 1 pN) forces from seed 0,
+    10 steps at tolerance 1e-8 with the iteration cap 50: the same iterates as the
+    FP64 oracle (the FP64 path differs from it only by rounding order)."""
+    h = make_handle(npfem, 258, "fp64", tol=1e-8, max_iter=50, armijo_noise=0.0)
+    m, _, _ = oracle_model(258)
+    p = W.population(258, 1, 0, forces="noise", noise_pN=1.0)
+    xo, vo, so = oracle_steps(m, p["x"], p["v"], p["f"], steps=10, tol=1e-8, max_iter=50)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"], steps=10, dtype="float64")
+    assert (sg["status"] == 0).all() and (sg["residual"] <= 1e-8).all()
+    assert max_rel_disp(xg, xo, m.lbar) <= 1e-10
+    assert max_rel_disp(DT * vg, DT * vo, m.lbar) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_graph_replay_matches_eager_steps(npfem, prec):
+    """Three steps captured as one CUDA graph and replayed equal three eager steps:
+    bitwise for the FP32 path (each cell's arithmetic does not depend on the block that
+    takes it), to the solver tolerance for BF16 (the idle-SM split between tensor-core
+    and SIMT blocks is dynamic)."""
+    import torch
+    m, rest, tris = oracle_model(642)
+    h = make_handle(npfem, 642, prec, tol=1e-6)
+    p = population32(642, 300, seed=80, forces="shear", noise_pN=0.5)
+    mk = lambda a: torch.tensor(W.to_soa(a), dtype=torch.float32, device="cuda")
+    xa, va, f = mk(p["x"]), mk(p["v"]), mk(p["f"])
+    xb, vb = xa.clone(), va.clone()
+    for _ in range(3):
+        npfem.step([h], [300], xa, va, f, DT)
+    g = npfem.StepGraph([h], [300], xb, vb, f, DT, steps=3)
+    assert torch.equal(xb, mk(p["x"]))  # creation does not touch the state
+    n0 = npfem.launch_count()
+    g.launch()
+    torch.cuda.synchronize()
+    assert npfem.launch_count() > n0
+    g.close()
+    if prec == "fp32":
+        assert torch.equal(xa, xb) and torch.equal(va, vb)
+    else:
+        assert max_rel_disp(W.from_soa(xa.double().cpu().numpy()), W.from_soa(xb.double().cpu().numpy()),
+                            m.lbar) <= 3e-5
