@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--precision", default="bf16")
     ap.add_argument("--warmstart", default="learned", choices=["learned", "none"])
     ap.add_argument("--ws-train-steps", type=int, default=3000)
+    ap.add_argument("--graph", type=int, default=1, help="1: each timed step replays a captured CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -210,7 +211,7 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------
 # GPU legs
 # ----------------------------------------------------------------------------------
-def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_times=False):
+def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_times=False, graph=False):
     xs = torch.tensor(W.to_soa(pop["x"][:cells]), dtype=torch.float32, device="cuda")
     vs = torch.tensor(W.to_soa(pop["v"][:cells]), dtype=torch.float32, device="cuda")
     fs = torch.tensor(W.to_soa(pop["f"][:cells]), dtype=torch.float32, device="cuda")
@@ -220,21 +221,30 @@ def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_tim
         N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
     torch.cuda.synchronize()
     if kernel_times:
-        handle.kernel_timing(steps)
+        # with a graph the event pair is captured and re-recorded by every replay
+        handle.kernel_timing(1 if graph else steps)
+    g = N.StepGraph([handle], [cells], xs, vs, fs, DT, steps=1, stats=st) if graph else None
+    kms = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    iters_all = []
     launches0 = N.launch_count()
     for k in range(steps):
         flush.zero_()  # writes a buffer larger than L2 between timed steps
         ev[k][0].record(stream)
-        N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
+        if g is not None:
+            g.launch(stream.cuda_stream)
+        else:
+            N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
         ev[k][1].record(stream)
+        if g is not None and kernel_times:
+            kms.append(handle.kernel_time_last())  # waits for this step
     torch.cuda.synchronize()
     launches = N.launch_count() - launches0
+    if g is not None:
+        g.close()
     times = [a.elapsed_time(b) for a, b in ev]
     ktimes = None
     if kernel_times:
-        ktimes = handle.kernel_times(steps)
+        ktimes = np.array(kms) if g is not None else handle.kernel_times(steps)
         handle.kernel_timing(0)
     # statistics of the last step (per-launch work for the roofline)
     s = st.cpu().numpy().view(N.CELL_STATS_DTYPE).reshape(cells)
@@ -299,7 +309,8 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        dl = device_leg(N, W, handle, pop, cells, args.steps, args.warmup, torch, flush, kernel_times=True)
+        dl = device_leg(N, W, handle, pop, cells, args.steps, args.warmup, torch, flush, kernel_times=True,
+                        graph=bool(args.graph))
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     barrier(pg)
@@ -361,6 +372,7 @@ def main():
                                        f"+ N(0,0.5 pN), dt 0.1 us, tol 1e-6",
                            "cells_per_gpu": cells, "precision": prec_name,
                            "warm_start": "learned MLP" if ws is not None else "first guess y", "lbfgs_m": m,
+                           "launch": "CUDA graph of one step per timed step" if args.graph else "npfem_step per step",
                            "l2": "flushed between timed steps (256 MB write)"},
                 "gpu_launches": dl["launches"],
                 "wall_s": t_wall,

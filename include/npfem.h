@@ -296,6 +296,12 @@ int npfem_kernel_timing(npfem_handle* h, int capacity);
    restarts the recording.  Errors: INVALID_ARG, CUDA. */
 int npfem_kernel_times(npfem_handle* h, float* ms_out, int max, int* count);
 
+/* Duration in ms of the first recorded solver launch pair (synchronises on it, keeps
+   the recording): with a CUDA graph captured while timing was on, the pair is
+   re-recorded by every replay, so this reads the latest replay.
+   Errors: INVALID_ARG (nothing recorded), CUDA. */
+int npfem_kernel_time_last(npfem_handle* h, float* ms);
+
 /* Number of kernels the library has launched in this process (all devices, all
    entry points), for counting device work; thread-safe, never fails. */
 unsigned long long npfem_launch_count(void);

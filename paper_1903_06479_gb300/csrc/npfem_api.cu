@@ -518,6 +518,17 @@ int npfem_kernel_timing(npfem_handle* h, int capacity)
     return 0;
 }
 
+int npfem_kernel_time_last(npfem_handle* h, float* ms)
+{
+    if (!h || !ms) return fail(NPFEM_ERR_INVALID_ARG, "npfem_kernel_time_last: bad argument");
+    DeviceGuard guard(h->device);
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (h->tev_used < 2) return fail(NPFEM_ERR_INVALID_ARG, "npfem_kernel_time_last: nothing recorded");
+    NPFEM_CUDA(cudaEventSynchronize(h->tev[1]));
+    NPFEM_CUDA(cudaEventElapsedTime(ms, h->tev[0], h->tev[1]));
+    return 0;
+}
+
 int npfem_kernel_times(npfem_handle* h, float* ms_out, int max, int* count)
 {
     if (!h || !count || max < 0 || (max > 0 && !ms_out)) return fail(NPFEM_ERR_INVALID_ARG, "npfem_kernel_times: bad argument");

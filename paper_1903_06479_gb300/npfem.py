@@ -52,7 +52,7 @@ EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", 
            "npfem_check_device", "npfem_mlp_nparam", "npfem_ws_features", "npfem_mlp_loss_grad", "npfem_mlp_adam",
            "npfem_mlp_predict", "npfem_set_warmstart", "npfem_ws_guess", "npfem_launch_count",
            "npfem_kernel_timing", "npfem_kernel_times", "npfem_graph_create", "npfem_graph_launch",
-           "npfem_graph_destroy")
+           "npfem_graph_destroy", "npfem_kernel_time_last")
 
 
 def lib_path() -> str:
@@ -69,6 +69,7 @@ def lib():
         L.npfem_graph_create.argtypes = [vp, i32, vp, vp, vp, vp, C.c_double, i32, vp, C.POINTER(vp)]
         L.npfem_graph_launch.argtypes = [vp, vp]
         L.npfem_graph_destroy.argtypes = [vp]
+        L.npfem_kernel_time_last.argtypes = [vp, vp]
         L.npfem_kernel_timing.argtypes = [vp, i32]
         L.npfem_kernel_times.argtypes = [vp, vp, i32, vp]
         L.npfem_launch_count.argtypes = []
@@ -202,6 +203,12 @@ class Handle:
     def kernel_timing(self, capacity: int):
         """Record the solver-kernel time of the next `capacity` steps (0: stop)."""
         _check(lib().npfem_kernel_timing(self._h, int(capacity)))
+
+    def kernel_time_last(self) -> float:
+        """Duration (ms) of the first recorded solver launch pair (latest graph replay)."""
+        ms = C.c_float(0.0)
+        _check(lib().npfem_kernel_time_last(self._h, C.addressof(ms)))
+        return float(ms.value)
 
     def kernel_times(self, max_n: int = 4096) -> np.ndarray:
         """Durations (ms) of the recorded solver launches; restarts the recording."""
