@@ -269,6 +269,19 @@ int npfem_check_device(npfem_handle* h);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* npfem_last_error(void);
 
+/* Launch-shape autotuner: for every group (cells_per_group[g] > 0) times
+   `trial_steps` steps of that group alone (after one untimed step) on copies of its
+   x, v for each candidate shape, and keeps the fastest in the handle:
+   SIMT blocks of 512 or 640 threads (640 for FP32 state only), and for NPFEM_PREC_BF16
+   meshes of at most 960 vertices the tensor-core cluster kernel with and without the
+   idle-SM SIMT launch.  x, v are not modified.  Blocks.  Errors: INVALID_ARG, CUDA, OOM. */
+int npfem_autotune(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, const void* x,
+                   const void* v, const void* f_ext, double dt, int trial_steps);
+
+/* The launch shape a handle uses: *use_tc (cluster kernel), *threads (SIMT block
+   size), *fill_idle_sms.  Errors: INVALID_ARG. */
+int npfem_get_tuning(const npfem_handle* h, int* use_tc, int* threads, int* fill_idle_sms);
+
 /* A CUDA graph of `steps` consecutive npfem_step calls on fixed state buffers (the
    batching pattern of a time loop: the whole step, warm start and solver launches
    included, replays as one graph launch).  Creation runs one step on temporary copies

@@ -230,7 +230,8 @@ int check_opts(const npfem_opts* o)
 template <typename T>
 int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T* x, T* v, const T* f, const T* y,
               T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream,
-              const T* u0 = nullptr)
+              const T* u0 = nullptr, const long long* state_offs = nullptr, const long long* stats_offs = nullptr,
+              int threads = 0)
 {
     npfem_handle* h0 = meshes[0];
     LaunchArgs<T> a;
@@ -243,7 +244,8 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
         GroupDesc<T>& g = a.g[gi];
         g.topo = *reinterpret_cast<const TopoDev<T>*>(sizeof(T) == 4 ? (const void*)&h->tf : (const void*)&h->td);
         g.cell_begin = total;
-        g.state_off = state;
+        g.state_off = state_offs ? state_offs[gi] : state;
+        g.stats_off = stats_offs ? stats_offs[gi] : total;
         g.cells = cells[gi];
         long long sb = 0;
         place_vectors(&g, h->n_pad, h->nt, h0->opts.lbfgs_m, budget, &sb);
@@ -268,10 +270,13 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     a.p.contraction = CONTRACT_SIMT;
     a.u0 = u0;
 
-    const int threads = h0->threads;
+    if (threads <= 0) threads = h0->threads;
+    if (sizeof(T) == 8) threads = std::min(threads, 512);
     const int smem = kFixedSmem + smem_max;
     NPFEM_CUDA(set_cell_kernel_smem<T>(smem));
-    const int per_sm = smem > h0->smem_optin / 2 ? 1 : (smem > h0->smem_optin / 3 ? 2 : 3);
+    int per_sm = 1;
+    NPFEM_CUDA(cells_per_sm<T>(threads, smem, &per_sm));
+    per_sm = std::max(per_sm, 1);
     long long grid = std::min<long long>(total, (long long)h0->sm_count * per_sm);
     a.slot_bytes = slot;
     if (slot > 0) {
@@ -329,7 +334,7 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     int smem = kFixedSmem + g.smem_bytes;
     smem = std::max(smem, h->smem_optin / 2 + 4096);
     if (h->tc_smem != smem) {
-        NPFEM_CUDA(query_cells_tc(cluster, h->threads, smem, &h->tc_max_clusters));
+        NPFEM_CUDA(query_cells_tc(cluster, kTcThreads, smem, &h->tc_max_clusters));
         h->tc_smem = smem;
     }
     const int max_clusters = h->tc_max_clusters;
@@ -381,7 +386,7 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
         }
         NPFEM_CUDA(cudaEventRecord(h->ev_fork, stream));
     }
-    NPFEM_CUDA(launch_cells_tc(a, cluster, h->threads, smem, grid, stream));
+    NPFEM_CUDA(launch_cells_tc(a, cluster, kTcThreads, smem, grid, stream));
     if (helper > 0) {
         cudaError_t e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
         if (e == cudaSuccess) e = set_cell_kernel_smem<float>(smem_b);
@@ -399,32 +404,59 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     return 0;
 }
 
-// The solver launches of one step (tensor-core kernel per group when every group fits
-// it in BF16, else one SIMT launch over all groups).
+// The solver launches of one step: one cluster launch per group that takes the
+// tensor-core kernel (BF16, mesh of at most kTcMaxVerts vertices, not tuned away), and
+// one persistent SIMT launch per block size over the other groups.
 int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
                 const void* f_ext, cudaStream_t s, npfem_cell_stats* stats, const float* u0)
 {
-    if (meshes[0]->precision == NPFEM_PREC_BF16) {
-        bool all_tc = true;
-        for (int g = 0; g < n_groups; ++g) all_tc = all_tc && meshes[g]->n <= kTcMaxVerts;
-        if (all_tc) {
-            long long cell0 = 0, state0 = 0;
-            for (int g = 0; g < n_groups; ++g) {
-                int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + state0, (float*)v + state0,
-                                      (const float*)f_ext + state0, stats ? stats + cell0 : nullptr, s,
-                                      u0 ? u0 + state0 : nullptr);
-                if (rc) return rc;
-                cell0 += cells_per_group[g];
-                state0 += 3LL * meshes[g]->n * cells_per_group[g];
-            }
-            return 0;
+    const int prec = meshes[0]->precision;
+    std::vector<long long> soff(n_groups), coff(n_groups);
+    long long st = 0, ct = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        soff[g] = st;
+        coff[g] = ct;
+        st += 3LL * meshes[g]->n * cells_per_group[g];
+        ct += cells_per_group[g];
+    }
+    std::vector<char> done(n_groups, 0);
+    for (int g = 0; g < n_groups; ++g) {
+        if (cells_per_group[g] == 0) {
+            done[g] = 1;
+            continue;
+        }
+        if (prec == NPFEM_PREC_BF16 && meshes[g]->n <= kTcMaxVerts && meshes[g]->use_tc) {
+            int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + soff[g], (float*)v + soff[g],
+                                  (const float*)f_ext + soff[g], stats ? stats + coff[g] : nullptr, s,
+                                  u0 ? u0 + soff[g] : nullptr);
+            if (rc) return rc;
+            done[g] = 1;
         }
     }
-    if (meshes[0]->precision == NPFEM_PREC_FP64)
-        return run_cells<double>(meshes, n_groups, cells_per_group, (double*)x, (double*)v, (const double*)f_ext,
-                                 nullptr, nullptr, nullptr, stats, 0, s);
-    return run_cells<float>(meshes, n_groups, cells_per_group, (float*)x, (float*)v, (const float*)f_ext, nullptr,
-                            nullptr, nullptr, stats, 0, s, u0);
+    for (int g0 = 0; g0 < n_groups; ++g0) {
+        if (done[g0]) continue;
+        const int threads = prec == NPFEM_PREC_FP64 ? 512 : meshes[g0]->threads;
+        std::vector<npfem_handle*> hs;
+        std::vector<int32_t> cs;
+        std::vector<long long> so, co;
+        for (int g = g0; g < n_groups; ++g) {
+            if (done[g] || (prec != NPFEM_PREC_FP64 && meshes[g]->threads != threads)) continue;
+            hs.push_back(meshes[g]);
+            cs.push_back(cells_per_group[g]);
+            so.push_back(soff[g]);
+            co.push_back(coff[g]);
+            done[g] = 1;
+        }
+        int rc;
+        if (prec == NPFEM_PREC_FP64)
+            rc = run_cells<double>(hs.data(), (int)hs.size(), cs.data(), (double*)x, (double*)v, (const double*)f_ext,
+                                   nullptr, nullptr, nullptr, stats, 0, s, nullptr, so.data(), co.data(), threads);
+        else
+            rc = run_cells<float>(hs.data(), (int)hs.size(), cs.data(), (float*)x, (float*)v, (const float*)f_ext,
+                                  nullptr, nullptr, nullptr, stats, 0, s, u0, so.data(), co.data(), threads);
+        if (rc) return rc;
+    }
+    return 0;
 }
 
 // Learned first increments of every group with a warm start, into meshes[0]'s
@@ -516,6 +548,96 @@ int npfem_kernel_timing(npfem_handle* h, int capacity)
         h->tev.push_back(e);
     }
     return 0;
+}
+
+int npfem_get_tuning(const npfem_handle* h, int* use_tc, int* threads, int* fill_idle_sms)
+{
+    if (!h || !use_tc || !threads || !fill_idle_sms) return fail(NPFEM_ERR_INVALID_ARG, "npfem_get_tuning: null argument");
+    *use_tc = h->use_tc && h->precision == NPFEM_PREC_BF16 && h->n <= kTcMaxVerts;
+    *threads = h->threads;
+    *fill_idle_sms = h->opts.fill_idle_sms;
+    return 0;
+}
+
+int npfem_autotune(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, const void* x,
+                   const void* v, const void* f_ext, double dt, int trial_steps)
+{
+    if (int rc = validate_group(meshes, n_groups, cells_per_group)) return rc;
+    if (!x || !v || !f_ext || trial_steps < 1) return fail(NPFEM_ERR_INVALID_ARG, "npfem_autotune: bad argument");
+    DeviceGuard guard(meshes[0]->device);
+    NPFEM_CUDA(cudaDeviceSynchronize());
+    const int prec = meshes[0]->precision;
+    const size_t es = prec == NPFEM_PREC_FP64 ? 8 : 4;
+    struct Shape {
+        int use_tc, threads, fill;
+    };
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NPFEM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    NPFEM_CUDA(cudaEventCreate(&e0));
+    NPFEM_CUDA(cudaEventCreate(&e1));
+    int rc = 0;
+    size_t off = 0;
+    for (int g = 0; g < n_groups && !rc; ++g) {
+        npfem_handle* h = meshes[g];
+        const int cells = cells_per_group[g];
+        const size_t bytes = (size_t)3 * h->n * cells * es;
+        if (cells == 0) continue;
+        std::vector<Shape> cand;
+        cand.push_back({0, 512, h->opts.fill_idle_sms});
+        if (prec != NPFEM_PREC_FP64) cand.push_back({0, 640, h->opts.fill_idle_sms});
+        if (prec == NPFEM_PREC_BF16 && h->n <= kTcMaxVerts) {
+            cand.push_back({1, 512, 1});
+            cand.push_back({1, 512, 0});
+            cand.push_back({1, 640, 1});
+        }
+        void *tx = nullptr, *tv = nullptr;
+        cudaError_t ce = cudaMalloc(&tx, bytes);
+        if (ce == cudaSuccess) ce = cudaMalloc(&tv, bytes);
+        if (ce != cudaSuccess) {
+            rc = fail(ce == cudaErrorMemoryAllocation ? NPFEM_ERR_OOM : NPFEM_ERR_CUDA, "npfem_autotune: trial buffers");
+        }
+        float best = 1e30f;
+        Shape pick = {h->use_tc, h->threads, h->opts.fill_idle_sms};
+        for (const Shape& c : cand) {
+            if (rc) break;
+            h->use_tc = c.use_tc;
+            h->threads = c.threads;
+            h->opts.fill_idle_sms = c.fill;
+            const char* xs = static_cast<const char*>(x) + off;
+            const char* vs = static_cast<const char*>(v) + off;
+            const void* fs = static_cast<const char*>(f_ext) + off;
+            float total = 0.f;
+            for (int k = 0; k <= trial_steps && !rc; ++k) {
+                if (k == 0) {
+                    NPFEM_CUDA(cudaMemcpyAsync(tx, xs, bytes, cudaMemcpyDeviceToDevice, s));
+                    NPFEM_CUDA(cudaMemcpyAsync(tv, vs, bytes, cudaMemcpyDeviceToDevice, s));
+                }
+                NPFEM_CUDA(cudaEventRecord(e0, s));
+                npfem_handle* one[1] = {h};
+                rc = npfem_step(one, 1, &cells, tx, tv, fs, dt, s, nullptr);
+                NPFEM_CUDA(cudaEventRecord(e1, s));
+                NPFEM_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                NPFEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (k > 0) total += ms;
+            }
+            if (!rc && total < best) {
+                best = total;
+                pick = c;
+            }
+        }
+        h->use_tc = pick.use_tc;
+        h->threads = pick.threads;
+        h->opts.fill_idle_sms = pick.fill;
+        if (tx) cudaFree(tx);
+        if (tv) cudaFree(tv);
+        off += bytes;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    return rc;
 }
 
 int npfem_kernel_time_last(npfem_handle* h, float* ms)

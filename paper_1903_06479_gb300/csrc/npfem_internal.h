@@ -79,6 +79,7 @@ struct GroupDesc {
     TopoDev<T> topo;
     long long cell_begin;  // first global work item of the group
     long long state_off;   // element offset of the group's first cell in x / v / f
+    long long stats_off;   // index of the group's first cell in stats (and eval parts)
     int cells;
     int smem_bytes;        // dynamic smem this group needs (after kFixedSmem)
     int loc[kMaxVecs];     // >= 0: byte offset in smem; < 0: -(byte offset in the CTA's global slot) - 1
@@ -169,6 +170,9 @@ template <typename T>
 cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s);
 template <typename T>
 cudaError_t set_cell_kernel_smem(int bytes);
+// Resident SIMT blocks per SM at this block size and dynamic shared memory.
+template <typename T>
+cudaError_t cells_per_sm(int block, int smem, int* n);
 // Tensor-core kernel (BF16, A^-1 row blocks resident in TMEM across a cluster): sets
 // its shared-memory size and returns how many clusters can be resident at once.
 cudaError_t query_cells_tc(int cluster, int block, int smem, int* max_clusters);
@@ -181,6 +185,7 @@ cudaError_t launch_ws_increments(const npfem_handle* h, int n_cells, const float
 // Largest mesh the tensor-core path takes: A block (kpad / 2 columns) plus a
 // 32-column accumulator within 512 TMEM columns, and at most 8 blocks per cluster.
 constexpr int kTcMaxVerts = 960;
+constexpr int kTcThreads = 512;  // block size of the cluster kernel
 
 // Records msg as the calling thread's last error and returns code (npfem_api.cu).
 int set_error(int code, const std::string& msg);
@@ -257,7 +262,8 @@ struct npfem_handle {
     float* ws_u = nullptr;  // learned first increments of the cluster kernel's cells
     size_t ws_u_len = 0;
     int sm_count = 0, smem_optin = 0;
-    int threads = 512;
+    int threads = 512;  // SIMT block size (512 or 640 for FP32 state)
+    int use_tc = 1;     // BF16: use the tensor-core cluster kernel when the mesh fits it
     // buffers of npfem_step_host
     float* mlp = nullptr;       // learned warm start parameters on the device (weights BF16-rounded)
     void* hx = nullptr;

@@ -1132,8 +1132,8 @@ __device__ __forceinline__ void release_counters(unsigned int* work, int total_b
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512, 1) cell_kernel(const __grid_constant__ LaunchArgs<T> a)
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) cell_kernel(const __grid_constant__ LaunchArgs<T> a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     CellSolver<T> S;
@@ -1143,7 +1143,7 @@ __global__ void __launch_bounds__(512, 1) cell_kernel(const __grid_constant__ La
         int gi = 0;
         while (gi + 1 < a.n_groups && item >= a.g[gi + 1].cell_begin) ++gi;
         S.bind(a, a.g[gi], smem);
-        if (!S.begin(item - a.g[gi].cell_begin, item)) continue;
+        if (!S.begin(item - a.g[gi].cell_begin, a.g[gi].stats_off + item - a.g[gi].cell_begin)) continue;
         const TopoDev<T>& tp = a.g[gi].topo;
         while (S.wants_direction()) {
             S.first_loop();
@@ -1501,16 +1501,36 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
 
 }  // namespace
 
+// SIMT kernel variants by block size: 512 threads (128 registers) and, for FP32, 640
+// threads (96 registers; fills the vertex passes of 642-vertex cells in one round).
 template <typename T>
 cudaError_t set_cell_kernel_smem(int bytes)
 {
-    return cudaFuncSetAttribute(cell_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(cell_kernel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && sizeof(T) == 4)
+        e = cudaFuncSetAttribute(cell_kernel<float, 640>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+template <typename T>
+cudaError_t cells_per_sm(int block, int smem, int* n)
+{
+    if (block <= 512) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, cell_kernel<T, 512>, block, smem);
+    if constexpr (sizeof(T) == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, cell_kernel<float, 640>, block, smem);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
 cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s)
 {
-    cell_kernel<T><<<grid, block, smem, s>>>(a);
+    if (block <= 512) {
+        cell_kernel<T, 512><<<grid, block, smem, s>>>(a);
+    } else if constexpr (sizeof(T) == 4) {
+        if (block > 640) return cudaErrorInvalidValue;
+        cell_kernel<float, 640><<<grid, block, smem, s>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     count_launch();
     return cudaGetLastError();
 }
@@ -1565,6 +1585,8 @@ cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, 
 template cudaError_t set_cell_kernel_smem<float>(int);
 template cudaError_t set_cell_kernel_smem<double>(int);
 template cudaError_t launch_cells<float>(const LaunchArgs<float>&, int, int, int, cudaStream_t);
+template cudaError_t cells_per_sm<float>(int, int, int*);
+template cudaError_t cells_per_sm<double>(int, int, int*);
 template cudaError_t launch_cells<double>(const LaunchArgs<double>&, int, int, int, cudaStream_t);
 
 }  // namespace npfem

@@ -52,7 +52,7 @@ EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", 
            "npfem_check_device", "npfem_mlp_nparam", "npfem_ws_features", "npfem_mlp_loss_grad", "npfem_mlp_adam",
            "npfem_mlp_predict", "npfem_set_warmstart", "npfem_ws_guess", "npfem_launch_count",
            "npfem_kernel_timing", "npfem_kernel_times", "npfem_graph_create", "npfem_graph_launch",
-           "npfem_graph_destroy", "npfem_kernel_time_last")
+           "npfem_graph_destroy", "npfem_kernel_time_last", "npfem_autotune", "npfem_get_tuning")
 
 
 def lib_path() -> str:
@@ -70,6 +70,8 @@ def lib():
         L.npfem_graph_launch.argtypes = [vp, vp]
         L.npfem_graph_destroy.argtypes = [vp]
         L.npfem_kernel_time_last.argtypes = [vp, vp]
+        L.npfem_autotune.argtypes = [vp, i32, vp, vp, vp, vp, C.c_double, i32]
+        L.npfem_get_tuning.argtypes = [vp, vp, vp, vp]
         L.npfem_kernel_timing.argtypes = [vp, i32]
         L.npfem_kernel_times.argtypes = [vp, vp, i32, vp]
         L.npfem_launch_count.argtypes = []
@@ -204,6 +206,12 @@ class Handle:
         """Record the solver-kernel time of the next `capacity` steps (0: stop)."""
         _check(lib().npfem_kernel_timing(self._h, int(capacity)))
 
+    def tuning(self) -> dict:
+        """The launch shape this handle uses (npfem_get_tuning)."""
+        t, th, fi = C.c_int(0), C.c_int(0), C.c_int(0)
+        _check(lib().npfem_get_tuning(self._h, C.addressof(t), C.addressof(th), C.addressof(fi)))
+        return {"tensor_core": bool(t.value), "simt_threads": th.value, "fill_idle_sms": bool(fi.value)}
+
     def kernel_time_last(self) -> float:
         """Duration (ms) of the first recorded solver launch pair (latest graph replay)."""
         ms = C.c_float(0.0)
@@ -234,6 +242,16 @@ def step(handles, cells_per_group, x, v, f, dt: float, stream=None, stats=None):
     cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
     _check(lib().npfem_step(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), _addr(stream),
                             _addr(stats)))
+
+
+def autotune(handles, cells_per_group, x, v, f, dt: float, trial_steps: int = 2):
+    """npfem_autotune: picks each handle's launch shape by timing trial steps on copies
+    of its cells; returns the chosen shapes."""
+    handles = list(handles)
+    arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
+    _check(lib().npfem_autotune(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), int(trial_steps)))
+    return [h.tuning() for h in handles]
 
 
 class StepGraph:

@@ -9,9 +9,17 @@ from paper_1903_06479_gb300 import workloads as W
 DT = 0.1  # us
 
 
+_MODELS = {}
+
+
 def oracle_model(n_verts, **mat):
-    rest, tris = W.discocyte(n_verts)
-    return O.Model(rest, tris, W.material_vector(**mat), DT), rest, tris
+    """Oracle model of the discocyte mesh (cached: the FP64 set-up of large meshes
+    factors a dense matrix)."""
+    key = (n_verts, tuple(sorted(mat.items())))
+    if key not in _MODELS:
+        rest, tris = W.discocyte(n_verts)
+        _MODELS[key] = (O.Model(rest, tris, W.material_vector(**mat), DT), rest, tris)
+    return _MODELS[key]
 
 
 def population32(n_verts, cells, seed, **kw):

@@ -142,12 +142,17 @@ def test_several_steps_fp32(npfem):
     assert max_rel_disp(xg, xo, m.lbar) <= 5e-5
 
 
-def test_mixed_resolutions_one_launch(npfem):
+@pytest.mark.parametrize("prec,tune", [("fp32", False), ("bf16", False), ("bf16", True)])
+def test_mixed_resolutions_one_step(npfem, prec, tune):
+    """One step over 2562-, 642- and 258-vertex groups: a single persistent SIMT launch
+    (FP32), cluster launches for the groups that fit the tensor-core kernel plus a SIMT
+    launch for the rest (BF16), and the same after the autotuner picked each group's
+    launch shape (which leaves x, v untouched)."""
     import torch
     sizes = [(2562, 2), (642, 3), (258, 3)]
     hs, ms, pops = [], [], []
     for k, (nv, c) in enumerate(sizes):
-        hs.append(make_handle(npfem, nv, "fp32", tol=1e-6))
+        hs.append(make_handle(npfem, nv, prec, tol=1e-6))
         ms.append(oracle_model(nv)[0])
         pops.append(population32(nv, c, seed=20 + k, forces="shear", noise_pN=0.5, box=6.0))
     flat = lambda key: np.concatenate([W.to_soa(p[key]).ravel() for p in pops])
@@ -156,6 +161,12 @@ def test_mixed_resolutions_one_launch(npfem):
     fs = torch.tensor(flat("f"), dtype=torch.float32, device="cuda")
     total = sum(c for _, c in sizes)
     st = torch.zeros((total, 32), dtype=torch.uint8, device="cuda")
+    if tune:
+        x0 = xs.clone()
+        shapes = npfem.autotune(hs, [c for _, c in sizes], xs, vs, fs, DT, trial_steps=1)
+        assert torch.equal(xs, x0)
+        assert not shapes[0]["tensor_core"]  # 2562 vertices do not fit the cluster kernel
+        assert all(sh["simt_threads"] in (512, 640) for sh in shapes)
     npfem.step(hs, [c for _, c in sizes], xs, vs, fs, DT, stats=st)
     torch.cuda.synchronize()
     sg = st.cpu().numpy().view(npfem.CELL_STATS_DTYPE).reshape(total)
