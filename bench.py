@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--warmstart", default="learned", choices=["learned", "none"])
     ap.add_argument("--ws-train-steps", type=int, default=3000)
     ap.add_argument("--graph", type=int, default=1, help="1: each timed step replays a captured CUDA graph")
+    ap.add_argument("--autotune", type=int, default=1, help="1: pick the launch shape by trial steps first")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -304,6 +305,16 @@ def main():
     ws = None
     if args.warmstart == "learned" and args.precision != "fp64":
         ws = train_warm_start(handle, rank, args.ws_train_steps)
+    shape = None
+    if args.autotune:
+        mk = lambda a: torch.tensor(W.to_soa(a), dtype=torch.float64 if args.precision == "fp64" else torch.float32,
+                                    device="cuda")
+        # trial steps from a state past the first few steps from rest (typical iteration counts)
+        tx, tv, tf = mk(pop["x"]), mk(pop["v"]), mk(pop["f"])
+        for _ in range(5):
+            N.step([handle], [cells], tx, tv, tf, DT)
+        shape = N.autotune([handle], [cells], tx, tv, tf, DT, trial_steps=4)[0]
+        del tx, tv, tf
 
     barrier(pg)
     torch.cuda.synchronize()
@@ -373,6 +384,7 @@ def main():
                            "cells_per_gpu": cells, "precision": prec_name,
                            "warm_start": "learned MLP" if ws is not None else "first guess y", "lbfgs_m": m,
                            "launch": "CUDA graph of one step per timed step" if args.graph else "npfem_step per step",
+                           "launch_shape": shape if shape is not None else "default",
                            "l2": "flushed between timed steps (256 MB write)"},
                 "gpu_launches": dl["launches"],
                 "wall_s": t_wall,

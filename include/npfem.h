@@ -270,13 +270,16 @@ int npfem_check_device(npfem_handle* h);
 const char* npfem_last_error(void);
 
 /* Launch-shape autotuner: for every group (cells_per_group[g] > 0) times
-   `trial_steps` steps of that group alone (after one untimed step) on copies of its
-   x, v for each candidate shape, and keeps the fastest in the handle:
+   `trial_steps` back-to-back steps of that group alone (after one untimed step) on
+   copies of its x, v for each candidate shape, and keeps the fastest in the handle:
    SIMT blocks of 512 or 640 threads (640 for FP32 state only), and for NPFEM_PREC_BF16
    meshes of at most 960 vertices the tensor-core cluster kernel with and without the
-   idle-SM SIMT launch.  x, v are not modified.  Blocks.  Errors: INVALID_ARG, CUDA, OOM. */
+   idle-SM SIMT launch.  x, v are not modified.  trial_ms (optional, 5 floats per
+   group) receives the mean trial-step time of each candidate in the order SIMT 512,
+   SIMT 640, clusters + idle-SM 512, clusters only, clusters + idle-SM 640 (-1 where
+   a candidate does not apply).  Blocks.  Errors: INVALID_ARG, CUDA, OOM. */
 int npfem_autotune(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, const void* x,
-                   const void* v, const void* f_ext, double dt, int trial_steps);
+                   const void* v, const void* f_ext, double dt, int trial_steps, float* trial_ms);
 
 /* The launch shape a handle uses: *use_tc (cluster kernel), *threads (SIMT block
    size), *fill_idle_sms.  Errors: INVALID_ARG. */

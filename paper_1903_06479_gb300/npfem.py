@@ -70,7 +70,7 @@ def lib():
         L.npfem_graph_launch.argtypes = [vp, vp]
         L.npfem_graph_destroy.argtypes = [vp]
         L.npfem_kernel_time_last.argtypes = [vp, vp]
-        L.npfem_autotune.argtypes = [vp, i32, vp, vp, vp, vp, C.c_double, i32]
+        L.npfem_autotune.argtypes = [vp, i32, vp, vp, vp, vp, C.c_double, i32, vp]
         L.npfem_get_tuning.argtypes = [vp, vp, vp, vp]
         L.npfem_kernel_timing.argtypes = [vp, i32]
         L.npfem_kernel_times.argtypes = [vp, vp, i32, vp]
@@ -250,8 +250,16 @@ def autotune(handles, cells_per_group, x, v, f, dt: float, trial_steps: int = 2)
     handles = list(handles)
     arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
     cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
-    _check(lib().npfem_autotune(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), int(trial_steps)))
-    return [h.tuning() for h in handles]
+    ms = np.zeros(5 * len(handles), dtype=np.float32)
+    _check(lib().npfem_autotune(arr, len(handles), cells, _addr(x), _addr(v), _addr(f), float(dt), int(trial_steps),
+                                ms.ctypes.data))
+    names = ("simt512", "simt640", "tc_fill512", "tc_only", "tc_fill640")
+    out = []
+    for g, h in enumerate(handles):
+        t = h.tuning()
+        t["trial_ms"] = {nm: float(ms[5 * g + q]) for q, nm in enumerate(names) if ms[5 * g + q] >= 0}
+        out.append(t)
+    return out
 
 
 class StepGraph:
