@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--cells", type=int, default=1024)
     ap.add_argument("--precision", default="bf16")
     ap.add_argument("--warmstart", default="learned", choices=["learned", "none"])
-    ap.add_argument("--ws-train-steps", type=int, default=3000)
+    ap.add_argument("--ws-train-steps", type=int, default=100000)
+    ap.add_argument("--ws-vertices", type=int, default=32, help="training vertices sampled per cell and step")
     ap.add_argument("--graph", type=int, default=1, help="1: each timed step replays a captured CUDA graph")
     ap.add_argument("--autotune", type=int, default=1, help="1: pick the launch shape by trial steps first")
     ap.add_argument("--no-e2e", action="store_true")
@@ -274,12 +275,13 @@ def e2e_leg(N, W, handle, pop, cells, steps, warmup, torch):
     return dt, 3 * nb, 2 * nb + 32 * cells
 
 
-def train_warm_start(handle, rank, train_steps):
+def train_warm_start(handle, rank, train_steps, vertices):
     """Trains the warm-start network on trajectories of the plain solver (1000 other
     cells, 200 steps, seed 100 + rank) and installs it; returns a summary."""
     from paper_1903_06479_gb300 import learn
     t0 = time.perf_counter()
-    P, info = learn.train_warmstart(handle, n_cells=1000, steps=200, seed=100 + rank, train_steps=train_steps)
+    P, info = learn.train_warmstart(handle, n_cells=1000, steps=200, seed=100 + rank, train_steps=train_steps,
+                                    vertices_per_step=vertices)
     handle.set_warmstart(P, 1)
     return {"train_s": time.perf_counter() - t0, "samples": info["samples"], "step_pairs": info["step_pairs"],
             "loss_init": info["loss_init"], "loss_final": info["loss_final"], "network": "9-64-64-3 tanh, BF16 operands"}
@@ -304,7 +306,7 @@ def main():
 
     ws = None
     if args.warmstart == "learned" and args.precision != "fp64":
-        ws = train_warm_start(handle, rank, args.ws_train_steps)
+        ws = train_warm_start(handle, rank, args.ws_train_steps, args.ws_vertices)
     shape = None
     if args.autotune:
         mk = lambda a: torch.tensor(W.to_soa(a), dtype=torch.float64 if args.precision == "fp64" else torch.float32,
