@@ -41,6 +41,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RBC-steps/s (642-vtx cells, equal accuracy), chosen vs plain form, % roofline"
+# DRAM bytes (read + write) per launch of the cluster kernel at 1024 cells, from
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of this code, keyed by
+# warm start.  Set to None when the kernel changes.
+NCU_TRAFFIC_TC = {"learned": 33.65e6, "none": 25.71e6}
 DT = 0.1
 N_VERTS = 642
 
@@ -361,8 +365,11 @@ def main():
     t_kernel = float(np.mean(kms)) / 1e3 if kms is not None and len(kms) else dev_s / args.steps
     achieved = alg / t_kernel / 1e9
     kname = "cell_kernel_tc<float>" if args.precision == "bf16" else "cell_kernel"
+    traffic = None
+    if args.precision == "bf16" and cells == 1024 and NCU_TRAFFIC_TC is not None:
+        traffic = NCU_TRAFFIC_TC.get("learned" if ws is not None else "none")
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_source": f"{pk_kind} (HBM copy bandwidth, MEASURED_PEAKS.json)" if pk_kind == "measured" else pk_kind,
             "kernel": kname, "kernel_ms_mean": t_kernel * 1e3, "algorithmic_bytes_per_launch": alg}
 

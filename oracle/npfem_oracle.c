@@ -8,7 +8,7 @@
  * Method: Kotsalos, Latt & Chopard, "Bridging the computational gap between
  * mesoscopic and continuum modeling of red blood cells for fully resolved blood
  * flow", arXiv:1903.06479.  Every function below names the section / equation it
- * follows.  Readings where the paper is silent are listed in the design doc and are
+ * follows.  Where the paper is silent, the choice made is stated in place and
  * marked "reading" in the comments.  The code favours the literal form over speed:
  * dense n x n matrices, a dense Cholesky factor of the constant Hessian
  * approximation (never its inverse), an explicit 2x2 eigen-solve for the principal
