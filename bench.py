@@ -378,8 +378,10 @@ def main():
         cores = os.cpu_count() or 1
         sample_cells = min(64, cells)
         t = oracle_sample(pop, sample_cells, 10, cores)
+        t1 = oracle_sample(pop, 8, 5, 1)
         cpu = {"value": sample_cells * 10 / t, "unit": "RBC-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{sample_cells} cells x 10 time steps of the same workload, FP64, {cores} threads"}
+               "sample": f"{sample_cells} cells x 10 time steps of the same workload, FP64, {cores} threads",
+               "value_1core": 8 * 5 / t1, "sample_1core": "8 cells x 5 time steps, 1 thread"}
 
     if rank == 0:
         prec_name = {"bf16": "BF16 tensor-core A^-1 contraction, FP32 elsewhere", "fp32": "FP32",
