@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--cells", type=int, default=1024)
     ap.add_argument("--precision", default="bf16")
     ap.add_argument("--warmstart", default="learned", choices=["learned", "none"])
+    ap.add_argument("--history", type=int, default=1, help="1: temporal warm start from the previous step")
     ap.add_argument("--ws-train-steps", type=int, default=100000)
     ap.add_argument("--ws-vertices", type=int, default=32, help="training vertices sampled per cell and step")
     ap.add_argument("--graph", type=int, default=1, help="1: each timed step replays a captured CUDA graph")
@@ -304,7 +305,7 @@ def main():
     N.lib()
     cells = args.cells
     pop = W.population(N_VERTS, cells, seed=1 + rank, forces="shear", noise_pN=0.5)
-    opts = N.default_opts(precision=args.precision, tol=1e-6, max_iter=50, refine=0)
+    opts = N.default_opts(precision=args.precision, tol=1e-6, max_iter=50, refine=0, warm_history=args.history)
     handle = N.Handle(pop["rest"], pop["tris"], N.material(), opts, dt=DT, device=local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -340,8 +341,8 @@ def main():
 
     plain = None
     if not args.no_plain and (args.precision != "fp32" or ws is not None):
-        hp = N.Handle(pop["rest"], pop["tris"], N.material(), N.default_opts(precision="fp32", tol=1e-6, max_iter=50),
-                      dt=DT, device=local)
+        hp = N.Handle(pop["rest"], pop["tris"], N.material(),
+                      N.default_opts(precision="fp32", tol=1e-6, max_iter=50, warm_history=0), dt=DT, device=local)
         pl = device_leg(N, W, hp, pop, cells, args.steps, args.warmup, torch, flush)
         plain = {"value": total_cells * args.steps / max_over_ranks(pg, sum(pl["times"]) / 1e3),
                  "unit": "RBC-steps/s", "form": "FP32 SIMT contraction, first guess y", "steps": args.steps,
@@ -393,7 +394,9 @@ def main():
                 "config": {"workload": f"{cells} RBCs x 642-vertex discocyte per GPU, shear traction U(10,1000)/s "
                                        f"+ N(0,0.5 pN), dt 0.1 us, tol 1e-6",
                            "cells_per_gpu": cells, "precision": prec_name,
-                           "warm_start": "learned MLP" if ws is not None else "first guess y", "lbfgs_m": m,
+                           "warm_start": ("learned MLP" if ws is not None else "first guess y")
+                           + (" (first step), then previous step's correction" if args.history else ""),
+                           "lbfgs_m": m,
                            "launch": "CUDA graph of one step per timed step" if args.graph else "npfem_step per step",
                            "launch_shape": shape if shape is not None else "default",
                            "l2": "flushed between timed steps (256 MB write)"},

@@ -101,7 +101,13 @@ typedef struct {
    refine: NPFEM_PREC_BF16 only: refinement sweeps of the tensor-core A^-1
            contraction (0 or 1): r = A^-1 q, then r += A^-1 (q - H~ r).
    fill_idle_sms: NPFEM_PREC_BF16 only: 1 = SMs that the tensor-core clusters leave
-           idle run the SIMT solver on the same cells (dynamic split), 0 = clusters only. */
+           idle run the SIMT solver on the same cells (dynamic split), 0 = clusters only.
+   warm_history: 1 = temporal warm start: when a call steps the same groups and cell
+           counts as the previous call through meshes[0], each cell starts from
+           x^(1) = y + (x_n - y_{n-1}), its previous step's converged correction (kept
+           by the library, 12n bytes per cell in the state's type); the iteration still
+           runs to the residual tolerance, so stepping other cells in the same layout
+           only costs iterations.  0 = off.  Not used by npfem_step_static. */
 typedef struct {
     int32_t precision;
     int32_t lbfgs_m;
@@ -114,6 +120,7 @@ typedef struct {
     double armijo_noise;
     int32_t refine;
     int32_t fill_idle_sms;
+    int32_t warm_history;
 } npfem_opts;
 
 /* Per-cell result of one npfem_step call (device memory, 32 bytes). */

@@ -220,6 +220,8 @@ int check_opts(const npfem_opts* o)
     if (o->refine < 0 || o->refine > 1) return fail(NPFEM_ERR_INVALID_ARG, "opts.refine must be 0 or 1");
     if (o->fill_idle_sms < 0 || o->fill_idle_sms > 1)
         return fail(NPFEM_ERR_INVALID_ARG, "opts.fill_idle_sms must be 0 or 1");
+    if (o->warm_history < 0 || o->warm_history > 1)
+        return fail(NPFEM_ERR_INVALID_ARG, "opts.warm_history must be 0 or 1");
     if (o->precision == NPFEM_PREC_TF32)
         return fail(NPFEM_ERR_INVALID_ARG,
                     "NPFEM_PREC_TF32 is not available: a TF32 row block of A^-1 does not fit in tensor memory; "
@@ -231,7 +233,7 @@ template <typename T>
 int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T* x, T* v, const T* f, const T* y,
               T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream,
               const T* u0 = nullptr, const long long* state_offs = nullptr, const long long* stats_offs = nullptr,
-              int threads = 0)
+              int threads = 0, const T* hist_in = nullptr, T* hist_out = nullptr)
 {
     npfem_handle* h0 = meshes[0];
     LaunchArgs<T> a;
@@ -269,6 +271,8 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     a.p.mode = mode;
     a.p.contraction = CONTRACT_SIMT;
     a.u0 = u0;
+    a.hist_in = hist_in;
+    a.hist_out = hist_out;
 
     if (threads <= 0) threads = h0->threads;
     if (sizeof(T) == 8) threads = std::min(threads, 512);
@@ -299,12 +303,14 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
 
 // One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
 int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
-                 cudaStream_t stream, const float* u0)
+                 cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out)
 {
     if (cells == 0) return 0;
     LaunchArgs<float> a;
     memset(&a, 0, sizeof(a));
     a.u0 = u0;
+    a.hist_in = hist_in;
+    a.hist_out = hist_out;
     GroupDesc<float>& g = a.g[0];
     g.topo = h->tf;
     g.cell_begin = 0;
@@ -408,7 +414,8 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
 // tensor-core kernel (BF16, mesh of at most kTcMaxVerts vertices, not tuned away), and
 // one persistent SIMT launch per block size over the other groups.
 int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
-                const void* f_ext, cudaStream_t s, npfem_cell_stats* stats, const float* u0)
+                const void* f_ext, cudaStream_t s, npfem_cell_stats* stats, const float* u0, const void* hist_in,
+                void* hist_out)
 {
     const int prec = meshes[0]->precision;
     std::vector<long long> soff(n_groups), coff(n_groups);
@@ -428,7 +435,8 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
         if (prec == NPFEM_PREC_BF16 && meshes[g]->n <= kTcMaxVerts && meshes[g]->use_tc) {
             int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + soff[g], (float*)v + soff[g],
                                   (const float*)f_ext + soff[g], stats ? stats + coff[g] : nullptr, s,
-                                  u0 ? u0 + soff[g] : nullptr);
+                                  u0 ? u0 + soff[g] : nullptr, hist_in ? (const float*)hist_in + soff[g] : nullptr,
+                                  hist_out ? (float*)hist_out + soff[g] : nullptr);
             if (rc) return rc;
             done[g] = 1;
         }
@@ -450,10 +458,12 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
         int rc;
         if (prec == NPFEM_PREC_FP64)
             rc = run_cells<double>(hs.data(), (int)hs.size(), cs.data(), (double*)x, (double*)v, (const double*)f_ext,
-                                   nullptr, nullptr, nullptr, stats, 0, s, nullptr, so.data(), co.data(), threads);
+                                   nullptr, nullptr, nullptr, stats, 0, s, nullptr, so.data(), co.data(), threads,
+                                   (const double*)hist_in, (double*)hist_out);
         else
             rc = run_cells<float>(hs.data(), (int)hs.size(), cs.data(), (float*)x, (float*)v, (const float*)f_ext,
-                                  nullptr, nullptr, nullptr, stats, 0, s, u0, so.data(), co.data(), threads);
+                                  nullptr, nullptr, nullptr, stats, 0, s, u0, so.data(), co.data(), threads,
+                                  (const float*)hist_in, (float*)hist_out);
         if (rc) return rc;
     }
     return 0;
@@ -527,6 +537,7 @@ void npfem_default_opts(npfem_opts* o)
     o->armijo_noise = 4.0;
     o->refine = 0;
     o->fill_idle_sms = 1;
+    o->warm_history = 1;
 }
 
 const char* npfem_last_error(void) { return g_last_error.c_str(); }
@@ -601,6 +612,8 @@ int npfem_autotune(npfem_handle* const* meshes, int n_groups, const int32_t* cel
         }
         float best = 1e30f;
         Shape pick = {h->use_tc, h->threads, h->opts.fill_idle_sms, -1};
+        const int hist_opt = h->opts.warm_history;
+        h->opts.warm_history = 0;  // every candidate starts from the same first iterates
         for (const Shape& c : cand) {
             if (rc) break;
             h->use_tc = c.use_tc;
@@ -631,6 +644,7 @@ int npfem_autotune(npfem_handle* const* meshes, int n_groups, const int32_t* cel
         h->use_tc = pick.use_tc;
         h->threads = pick.threads;
         h->opts.fill_idle_sms = pick.fill;
+        h->opts.warm_history = hist_opt;
         if (tx) cudaFree(tx);
         if (tv) cudaFree(tv);
         off += bytes;
@@ -792,18 +806,56 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
     DeviceGuard guard(meshes[0]->device);
     std::lock_guard<std::mutex> lk(meshes[0]->mu);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    npfem_handle* h0 = meshes[0];
+    // temporal warm start: read the last step's corrections when this call steps the
+    // same groups and cell counts, and write this step's
+    const void* hist_in = nullptr;
+    void* hist_out = nullptr;
+    if (h0->opts.warm_history) {
+        std::vector<long long> sig;
+        size_t elems = 0;
+        for (int g = 0; g < n_groups; ++g) {
+            sig.push_back(reinterpret_cast<long long>(meshes[g]));
+            sig.push_back(cells_per_group[g]);
+            elems += (size_t)3 * meshes[g]->n * cells_per_group[g];
+        }
+        const size_t bytes = elems * (h0->precision == NPFEM_PREC_FP64 ? 8 : 4);
+        if (bytes > h0->hist_bytes) {
+            if (h0->hist) {
+                NPFEM_CUDA(cudaStreamSynchronize(s));
+                cudaFree(h0->hist);
+                h0->hist = nullptr;
+                h0->hist_bytes = 0;
+                h0->hist_sig.clear();
+            }
+            NPFEM_CUDA(cudaMalloc(&h0->hist, bytes));
+            h0->hist_bytes = bytes;
+        }
+        if (bytes > 0) {
+            if (sig == h0->hist_sig) hist_in = h0->hist;
+            hist_out = h0->hist;
+            h0->hist_sig = sig;
+        }
+    }
     const float* u0 = nullptr;
-    if (meshes[0]->precision != NPFEM_PREC_FP64) {
+    if (meshes[0]->precision != NPFEM_PREC_FP64 && !hist_in) {
         if (int rc = precompute_warm_start(meshes, n_groups, cells_per_group, (const float*)x, (const float*)v,
                                            (const float*)f_ext, s, &u0))
             return rc;
     }
-    npfem_handle* h0 = meshes[0];
     const bool timed = h0->tev_used + 2 <= (int)h0->tev.size();
-    if (timed) NPFEM_CUDA(cudaEventRecord(h0->tev[h0->tev_used], s));
-    int rc = step_groups(meshes, n_groups, cells_per_group, x, v, f_ext, s, stats, u0);
+    unsigned rec_flags = cudaEventRecordDefault;
+    if (timed) {
+        // inside a stream capture the pair must become event-record nodes of the graph
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        NPFEM_CUDA(cudaStreamIsCapturing(s, &cap));
+        if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+        NPFEM_CUDA(cudaEventRecordWithFlags(h0->tev[h0->tev_used], s, rec_flags));
+    }
+    int rc = step_groups(meshes, n_groups, cells_per_group, x, v, f_ext, s, stats, u0, hist_in, hist_out);
+    if (rc) h0->hist_sig.clear();
     if (!rc && timed) {
-        NPFEM_CUDA(cudaEventRecord(h0->tev[h0->tev_used + 1], s));
+        NPFEM_CUDA(cudaEventRecordWithFlags(h0->tev[h0->tev_used + 1], s, rec_flags));
         h0->tev_used += 2;
     }
     return rc;

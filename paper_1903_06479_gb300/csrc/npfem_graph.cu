@@ -59,7 +59,11 @@ int npfem_graph_create(npfem_handle* const* meshes, int n_groups, const int32_t*
         if (e == cudaSuccess) e = cudaMemcpyAsync(tv, v, bytes, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) cuda_fail(e, "trial buffers");
     }
+    // the trial step records no kernel-timing events (those belong to the captured steps)
+    const int tev_used = meshes[0]->tev_used;
+    meshes[0]->tev_used = (int)meshes[0]->tev.size();
     if (!rc) rc = npfem_step(meshes, n_groups, cells_per_group, bytes ? tx : x, bytes ? tv : v, f_ext, dt, s, stats);
+    meshes[0]->tev_used = tev_used;
     if (!rc) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) cuda_fail(e, "trial step");

@@ -122,6 +122,8 @@ struct LaunchArgs {
     const T* y;        // eval mode: inertia target
     T* grad_out;       // eval mode
     const T* u0;       // precomputed learned first increments x^(1) - x_n ([3][n] per cell) or null
+    const T* hist_in;  // previous step's converged corrections x_n - y_{n-1} ([3][n] per cell) or null
+    T* hist_out;       // this step's corrections x_{n+1} - y_n are written here (or null)
     double* parts;     // eval mode: 8 doubles per cell
     npfem_cell_stats* stats;
     char* scratch;     // per-CTA global slots for vectors that do not fit in smem
@@ -261,6 +263,11 @@ struct npfem_handle {
     size_t scratch_bytes = 0;
     float* ws_u = nullptr;  // learned first increments of the cluster kernel's cells
     size_t ws_u_len = 0;
+    // temporal warm start: corrections of the last step (element type of the state),
+    // valid for the groups and cell counts recorded in hist_sig
+    void* hist = nullptr;
+    size_t hist_bytes = 0;
+    std::vector<long long> hist_sig;
     int sm_count = 0, smem_optin = 0;
     int threads = 512;  // SIMT block size (512 or 640 for FP32 state)
     int use_tc = 1;     // BF16: use the tensor-core cluster kernel when the mesh fits it
@@ -304,6 +311,10 @@ struct npfem_handle {
         if (ws_u) cudaFree(ws_u);
         ws_u = nullptr;
         ws_u_len = 0;
+        if (hist) cudaFree(hist);
+        hist = nullptr;
+        hist_bytes = 0;
+        hist_sig.clear();
         if (hx) cudaFree(hx);
         if (hv) cudaFree(hv);
         if (hf) cudaFree(hf);

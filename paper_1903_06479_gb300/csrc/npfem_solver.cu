@@ -600,8 +600,17 @@ struct CellSolver {
         }
         __syncthreads();
         // learned warm start: u = u_y + R MLP(features at y)
-        const int ws = (!eval_mode && T_.mlp) ? T_.ws_mode : 0;
-        if (ws && a->u0) {
+        // temporal warm start: u = u_y + (x_n - y_{n-1}) of this cell's previous step
+        const bool hist = !eval_mode && a->hist_in;
+        const int ws = (!eval_mode && !hist && T_.mlp) ? T_.ws_mode : 0;
+        if (hist) {
+            const T* Hc = a->hist_in + so;
+            for (int e = tid; e < N3; e += NT) {
+                const int c = e / np, i = e - c * np;
+                u[e] = i < n ? UYv[e] + Hc[c * n + i] : T(0);
+            }
+            __syncthreads();
+        } else if (ws && a->u0) {
             const T* U0 = a->u0 + so;
             for (int e = tid; e < N3; e += NT) {
                 const int c = e / np, i = e - c * np;
@@ -1071,6 +1080,14 @@ struct CellSolver {
                 const T vv = uc * inv_h;
                 v[c * n + i] = vv + kap * (vc[c] + wr[c] - vv);
                 x[c * n + i] = x[c * n + i] + uc;
+            }
+        }
+        if (a->hist_out) {
+            // the converged correction x_{n+1} - y_n for the next step's first iterate
+            T* Hc = a->hist_out + so;
+            for (int e = tid; e < 3 * n; e += NT) {
+                const int c = e / n, i = e - c * n;
+                Hc[e] = nonfinite ? T(0) : u[c * np + i] - UYv[c * np + i];
             }
         }
         if (tid == 0 && a->stats) {

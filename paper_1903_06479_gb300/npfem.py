@@ -35,7 +35,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("lbfgs_m", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("c1", C.c_double), ("c2", C.c_double), ("max_halvings", C.c_int32), ("fixed_alpha", C.c_int32),
                 ("equal_mass", C.c_int32), ("armijo_noise", C.c_double), ("refine", C.c_int32),
-                ("fill_idle_sms", C.c_int32)]
+                ("fill_idle_sms", C.c_int32), ("warm_history", C.c_int32)]
 
 
 class CellStats(C.Structure):

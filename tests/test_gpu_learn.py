@@ -123,7 +123,8 @@ def test_trained_network_cuts_iterations(npfem):
     import torch
     from paper_1903_06479_gb300 import learn
     rest, tris = W.discocyte(642)
-    h = npfem.Handle(rest, tris, npfem.material(), npfem.default_opts(precision="fp32", tol=1e-6), dt=DT)
+    h = npfem.Handle(rest, tris, npfem.material(), npfem.default_opts(precision="fp32", tol=1e-6, warm_history=0),
+                     dt=DT)
     P, info = learn.train_warmstart(h, n_cells=256, steps=60, seed=200, train_steps=1500)
     assert info["loss_final"] < 0.5 * info["loss_init"]
     # held-out cells, advanced 40 plain steps from rest, then one step each way

@@ -186,7 +186,9 @@ def test_mixed_resolutions_one_step(npfem, prec, tune):
 
 
 def test_step_host_matches_device(npfem):
-    h = make_handle(npfem, 642, "fp32", tol=1e-6)
+    # the same step twice from the same state: without the temporal warm start, which
+    # would start the second from the first one's answer
+    h = make_handle(npfem, 642, "fp32", tol=1e-6, warm_history=0)
     p = population32(642, 4, seed=5)
     xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
     xh = W.to_soa(p["x"]).astype(np.float32)
@@ -361,7 +363,7 @@ def test_single_cell_fp64_ten_steps(npfem):
     """One 258-vertex discocyte, FP64 on the GPU, i.i.d. N(0, 1 pN) forces from seed 0,
     10 steps at tolerance 1e-8 with the iteration cap 50: the same iterates as the
     FP64 oracle (the FP64 path differs from it only by rounding order)."""
-    h = make_handle(npfem, 258, "fp64", tol=1e-8, max_iter=50, armijo_noise=0.0)
+    h = make_handle(npfem, 258, "fp64", tol=1e-8, max_iter=50, armijo_noise=0.0, warm_history=0)
     m, _, _ = oracle_model(258)
     p = W.population(258, 1, 0, forces="noise", noise_pN=1.0)
     xo, vo, so = oracle_steps(m, p["x"], p["v"], p["f"], steps=10, tol=1e-8, max_iter=50)
@@ -379,7 +381,8 @@ def test_graph_replay_matches_eager_steps(npfem, prec):
     and SIMT blocks is dynamic)."""
     import torch
     m, rest, tris = oracle_model(642)
-    h = make_handle(npfem, 642, prec, tol=1e-6)
+    # eager and captured steps start from the same state: no temporal warm start
+    h = make_handle(npfem, 642, prec, tol=1e-6, warm_history=0)
     p = population32(642, 300, seed=80, forces="shear", noise_pN=0.5)
     mk = lambda a: torch.tensor(W.to_soa(a), dtype=torch.float32, device="cuda")
     xa, va, f = mk(p["x"]), mk(p["v"]), mk(p["f"])
@@ -398,3 +401,25 @@ def test_graph_replay_matches_eager_steps(npfem, prec):
     else:
         assert max_rel_disp(W.from_soa(xa.double().cpu().numpy()), W.from_soa(xb.double().cpu().numpy()),
                             m.lbar) <= 3e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_temporal_warm_start(npfem, prec):
+    """With warm_history each step starts from y + (x_n - y_{n-1}) of the same cell: the
+    steps still converge to the tolerance (positions against the FP64 oracle after 10
+    steps within the linear accumulation of the one-step bound) and take fewer
+    iterations than from y."""
+    steps = 10
+    m, _, _ = oracle_model(642)
+    p = population32(642, 8, seed=90, forces="shear", noise_pN=0.5)
+    if "temporal" not in _ORACLE:
+        _ORACLE["temporal"] = oracle_steps(m, p["x"], p["v"], p["f"], steps=steps, tol=1e-10, max_iter=200)[0]
+    xo = _ORACLE["temporal"]
+    its = {}
+    for hist in (0, 1):
+        h = make_handle(npfem, 642, prec, tol=1e-6, warm_history=hist)
+        xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"], steps=steps)
+        assert (sg["status"] == 0).all() and (sg["residual"] <= 1e-6).all()
+        assert max_rel_disp(xg, xo, m.lbar) <= steps * 1e-5 + fp32_store_allowance(p["x"], m.lbar)
+        its[hist] = sg["iterations"].mean()  # iterations of the last step
+    assert its[1] < its[0] - 1.0, its
