@@ -43,8 +43,8 @@ sys.path.insert(0, ROOT)
 METRIC = "RBC-steps/s (642-vtx cells, equal accuracy), chosen vs plain form, % roofline"
 # DRAM bytes (read + write) per launch of the cluster kernel at 1024 cells, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of this code, keyed by
-# warm start.  Set to None when the kernel changes.
-NCU_TRAFFIC_TC = {"learned": 33.65e6, "none": 25.71e6}
+# (warm start, temporal warm start).  Set to None when the kernel changes.
+NCU_TRAFFIC_TC = {("learned", 1): 33.63e6, ("learned", 0): 33.65e6, ("none", 0): 25.71e6}
 DT = 0.1
 N_VERTS = 642
 
@@ -368,7 +368,7 @@ def main():
     kname = "cell_kernel_tc<float>" if args.precision == "bf16" else "cell_kernel"
     traffic = None
     if args.precision == "bf16" and cells == 1024 and NCU_TRAFFIC_TC is not None:
-        traffic = NCU_TRAFFIC_TC.get("learned" if ws is not None else "none")
+        traffic = NCU_TRAFFIC_TC.get(("learned" if ws is not None else "none", args.history))
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_source": f"{pk_kind} (HBM copy bandwidth, MEASURED_PEAKS.json)" if pk_kind == "measured" else pk_kind,
