@@ -281,7 +281,8 @@ const char* npfem_last_error(void);
    copies of its x, v for each candidate shape, and keeps the fastest in the handle:
    SIMT blocks of 512 or 640 threads (640 for FP32 state only), and for NPFEM_PREC_BF16
    meshes of at most 960 vertices the tensor-core cluster kernel with and without the
-   idle-SM SIMT launch.  x, v are not modified.  trial_ms (optional, 5 floats per
+   idle-SM SIMT launch (with the handle's temporal warm start, as the steps that
+   follow will run).  x, v are not modified.  trial_ms (optional, 5 floats per
    group) receives the mean trial-step time of each candidate in the order SIMT 512,
    SIMT 640, clusters + idle-SM 512, clusters only, clusters + idle-SM 640 (-1 where
    a candidate does not apply).  Blocks.  Errors: INVALID_ARG, CUDA, OOM. */

@@ -613,7 +613,6 @@ int npfem_autotune(npfem_handle* const* meshes, int n_groups, const int32_t* cel
         float best = 1e30f;
         Shape pick = {h->use_tc, h->threads, h->opts.fill_idle_sms, -1};
         const int hist_opt = h->opts.warm_history;
-        h->opts.warm_history = 0;  // every candidate starts from the same first iterates
         for (const Shape& c : cand) {
             if (rc) break;
             h->use_tc = c.use_tc;
@@ -625,6 +624,7 @@ int npfem_autotune(npfem_handle* const* meshes, int n_groups, const int32_t* cel
             // one untimed step, then trial_steps back to back (as in a time loop)
             float total = 0.f;
             npfem_handle* one[1] = {h};
+            h->hist_sig.clear();  // each candidate's untimed step starts without history
             NPFEM_CUDA(cudaMemcpyAsync(tx, xs, bytes, cudaMemcpyDeviceToDevice, s));
             NPFEM_CUDA(cudaMemcpyAsync(tv, vs, bytes, cudaMemcpyDeviceToDevice, s));
             rc = npfem_step(one, 1, &cells, tx, tv, fs, dt, s, nullptr);
@@ -645,6 +645,7 @@ int npfem_autotune(npfem_handle* const* meshes, int n_groups, const int32_t* cel
         h->threads = pick.threads;
         h->opts.fill_idle_sms = pick.fill;
         h->opts.warm_history = hist_opt;
+        h->hist_sig.clear();
         if (tx) cudaFree(tx);
         if (tv) cudaFree(tv);
         off += bytes;
