@@ -207,8 +207,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RBC-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{cores} x 642-vertex RBCs per step (sample of the 1024-cell shear-flow "
-                                   f"population), tol 1e-6, dt 0.1 us"},
+            "config": {"workload": f"{args.cells} RBCs x 642-vertex discocyte per GPU, shear traction U(10,1000)/s "
+                                   f"+ N(0,0.5 pN), dt 0.1 us, tol 1e-6",
+                       "cells_per_gpu": args.cells, "precision": "FP64 (CPU oracle)",
+                       "timed_sample": f"{cores} of the cells, one time step each per timed step"},
             "cpu_baseline": {"value": value, "unit": "RBC-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{cores} cells x 1 time step per timed step, {args.steps} steps"},
             "e2e": {"value": value, "unit": "RBC-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
