@@ -44,7 +44,7 @@ METRIC = "RBC-steps/s (642-vtx cells, equal accuracy), chosen vs plain form, % r
 # DRAM bytes (read + write) per launch of the cluster kernel at 1024 cells, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of this code, keyed by
 # (warm start, temporal warm start).  Set to None when the kernel changes.
-NCU_TRAFFIC_TC = {("learned", 1): 33.63e6, ("learned", 0): 33.65e6, ("none", 0): 25.71e6}
+NCU_TRAFFIC_TC = {}
 DT = 0.1
 N_VERTS = 642
 
@@ -159,12 +159,14 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(n, m, stats_iters, stats_evals, cells):
+def algorithmic_bytes(n, m, stats_iters, stats_evals, cells, history=False):
     """Per-launch algorithmic bytes of the step (FP32): per cell 5*12n for x_n, v_n,
     F_ext in and x, v out; per iteration (4m + 6)*12n (the L-BFGS history streamed
-    twice, plus x, grad, d reads and s, y, x writes); per evaluation 2*12n."""
+    twice, plus x, grad, d reads and s, y, x writes); per evaluation 2*12n.  With the
+    temporal warm start, per cell 6*12n more: the last correction and the positions'
+    rounding residues with their FP32 values, each read and written."""
     vb = 12 * n
-    return cells * 5 * vb + stats_iters * (4 * m + 6) * vb + stats_evals * 2 * vb
+    return cells * (11 if history else 5) * vb + stats_iters * (4 * m + 6) * vb + stats_evals * 2 * vb
 
 
 def peaks():
@@ -363,7 +365,7 @@ def main():
 
     pk, pk_kind = peaks()
     m = opts.lbfgs_m
-    alg = algorithmic_bytes(N_VERTS, m, dl["iters"], dl["evals"], cells)
+    alg = algorithmic_bytes(N_VERTS, m, dl["iters"], dl["evals"], cells, history=bool(args.history))
     kms = dl["kernel_ms"]
     t_kernel = float(np.mean(kms)) / 1e3 if kms is not None and len(kms) else dev_s / args.steps
     achieved = alg / t_kernel / 1e9

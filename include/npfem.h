@@ -107,7 +107,13 @@ typedef struct {
            x^(1) = y + (x_n - y_{n-1}), its previous step's converged correction (kept
            by the library, 12n bytes per cell in the state's type); the iteration still
            runs to the residual tolerance, so stepping other cells in the same layout
-           only costs iterations.  0 = off.  Not used by npfem_step_static. */
+           only costs iterations.  With FP32 state the library also keeps, per
+           coordinate, the rounding error of storing x_{n+1} = x_n + u in FP32 and the
+           FP32 value it belongs to (24n more bytes per cell); the next such call adds
+           it back to every coordinate that still holds exactly that value, so that a
+           trajectory stepped call after call carries its positions to about twice FP32
+           precision (compensated summation).  A coordinate changed by the caller is
+           taken as stored.  0 = off.  Not used by npfem_step_static. */
 typedef struct {
     int32_t precision;
     int32_t lbfgs_m;

@@ -233,7 +233,7 @@ template <typename T>
 int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T* x, T* v, const T* f, const T* y,
               T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream,
               const T* u0 = nullptr, const long long* state_offs = nullptr, const long long* stats_offs = nullptr,
-              int threads = 0, const T* hist_in = nullptr, T* hist_out = nullptr)
+              int threads = 0, const T* hist_in = nullptr, T* hist_out = nullptr, long long pos_stride = 0)
 {
     npfem_handle* h0 = meshes[0];
     LaunchArgs<T> a;
@@ -273,6 +273,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     a.u0 = u0;
     a.hist_in = hist_in;
     a.hist_out = hist_out;
+    a.pos_stride = sizeof(T) == 4 && hist_out ? pos_stride : 0;
 
     if (threads <= 0) threads = h0->threads;
     if (sizeof(T) == 8) threads = std::min(threads, 512);
@@ -303,7 +304,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
 
 // One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
 int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
-                 cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out)
+                 cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out, long long pos_stride)
 {
     if (cells == 0) return 0;
     LaunchArgs<float> a;
@@ -311,6 +312,7 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     a.u0 = u0;
     a.hist_in = hist_in;
     a.hist_out = hist_out;
+    a.pos_stride = hist_out ? pos_stride : 0;
     GroupDesc<float>& g = a.g[0];
     g.topo = h->tf;
     g.cell_begin = 0;
@@ -415,7 +417,7 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
 // one persistent SIMT launch per block size over the other groups.
 int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
                 const void* f_ext, cudaStream_t s, npfem_cell_stats* stats, const float* u0, const void* hist_in,
-                void* hist_out)
+                void* hist_out, long long pos_stride)
 {
     const int prec = meshes[0]->precision;
     std::vector<long long> soff(n_groups), coff(n_groups);
@@ -436,7 +438,7 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
             int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + soff[g], (float*)v + soff[g],
                                   (const float*)f_ext + soff[g], stats ? stats + coff[g] : nullptr, s,
                                   u0 ? u0 + soff[g] : nullptr, hist_in ? (const float*)hist_in + soff[g] : nullptr,
-                                  hist_out ? (float*)hist_out + soff[g] : nullptr);
+                                  hist_out ? (float*)hist_out + soff[g] : nullptr, pos_stride);
             if (rc) return rc;
             done[g] = 1;
         }
@@ -463,7 +465,7 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
         else
             rc = run_cells<float>(hs.data(), (int)hs.size(), cs.data(), (float*)x, (float*)v, (const float*)f_ext,
                                   nullptr, nullptr, nullptr, stats, 0, s, u0, so.data(), co.data(), threads,
-                                  (const float*)hist_in, (float*)hist_out);
+                                  (const float*)hist_in, (float*)hist_out, pos_stride);
         if (rc) return rc;
     }
     return 0;
@@ -812,6 +814,7 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
     // same groups and cell counts, and write this step's
     const void* hist_in = nullptr;
     void* hist_out = nullptr;
+    long long pos_stride = 0;
     if (h0->opts.warm_history) {
         std::vector<long long> sig;
         size_t elems = 0;
@@ -820,7 +823,11 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
             sig.push_back(cells_per_group[g]);
             elems += (size_t)3 * meshes[g]->n * cells_per_group[g];
         }
-        const size_t bytes = elems * (h0->precision == NPFEM_PREC_FP64 ? 8 : 4);
+        // FP64: the corrections; FP32: the corrections, then the positions' rounding
+        // residues, then the FP32 positions they belong to (compensated positions)
+        const bool f32 = h0->precision != NPFEM_PREC_FP64;
+        pos_stride = f32 ? (long long)elems : 0;
+        const size_t bytes = elems * (f32 ? 3 * 4 : 8);
         if (bytes > h0->hist_bytes) {
             if (h0->hist) {
                 NPFEM_CUDA(cudaStreamSynchronize(s));
@@ -853,7 +860,7 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
         if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
         NPFEM_CUDA(cudaEventRecordWithFlags(h0->tev[h0->tev_used], s, rec_flags));
     }
-    int rc = step_groups(meshes, n_groups, cells_per_group, x, v, f_ext, s, stats, u0, hist_in, hist_out);
+    int rc = step_groups(meshes, n_groups, cells_per_group, x, v, f_ext, s, stats, u0, hist_in, hist_out, pos_stride);
     if (rc) h0->hist_sig.clear();
     if (!rc && timed) {
         NPFEM_CUDA(cudaEventRecordWithFlags(h0->tev[h0->tev_used + 1], s, rec_flags));

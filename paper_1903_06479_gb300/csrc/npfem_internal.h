@@ -124,6 +124,10 @@ struct LaunchArgs {
     const T* u0;       // precomputed learned first increments x^(1) - x_n ([3][n] per cell) or null
     const T* hist_in;  // previous step's converged corrections x_n - y_{n-1} ([3][n] per cell) or null
     T* hist_out;       // this step's corrections x_{n+1} - y_n are written here (or null)
+    // > 0 (FP32 with hist_out): the rounding residue of each stored position, the part of
+    // x_n + u below FP32 precision, sits at hist_out + pos_stride and the FP32 value it
+    // belongs to at hist_out + 2 pos_stride; hist_in != null marks both as this trajectory's
+    long long pos_stride;
     double* parts;     // eval mode: 8 doubles per cell
     npfem_cell_stats* stats;
     char* scratch;     // per-CTA global slots for vectors that do not fit in smem

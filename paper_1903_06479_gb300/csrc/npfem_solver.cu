@@ -579,14 +579,29 @@ struct CellSolver {
         so = gd->state_off + cell * 3LL * n;
         const T h = T_.h, inv_ms = T(1) / T_.inertia_scale;
         const bool eval_mode = a->p.mode == 1;
+        const bool hist = !eval_mode && a->hist_in;
         const T* x = a->x + so;
+        // compensated positions: x_n = x + residue while x holds exactly the value the
+        // last step stored (each coordinate checked), else x alone
+        const T* XLO = hist && a->pos_stride > 0 ? a->hist_in + a->pos_stride + so : nullptr;
+        const T* XHI = XLO ? XLO + a->pos_stride : nullptr;
         const T o0 = x[0], o1 = x[n], o2 = x[2 * n];
+        T l0 = T(0), l1 = T(0), l2 = T(0);
+        if (XLO) {
+            l0 = XHI[0] == o0 ? XLO[0] : T(0);
+            l1 = XHI[n] == o1 ? XLO[n] : T(0);
+            l2 = XHI[2 * n] == o2 ? XLO[2 * n] : T(0);
+        }
         for (int e = tid; e < N3; e += NT) {
             const int c = e / np, i = e - c * np;
             T xn = T(0), uy = T(0);
             if (i < n) {
                 const T xv = x[c * n + i];
                 xn = xv - (c == 0 ? o0 : (c == 1 ? o1 : o2));
+                if (XLO) {
+                    const T lv = XHI[c * n + i] == xv ? XLO[c * n + i] : T(0);
+                    xn += lv - (c == 0 ? l0 : (c == 1 ? l1 : l2));
+                }
                 if (eval_mode) {
                     uy = a->y[so + c * n + i] - xv;
                 } else {
@@ -601,7 +616,6 @@ struct CellSolver {
         __syncthreads();
         // learned warm start: u = u_y + R MLP(features at y)
         // temporal warm start: u = u_y + (x_n - y_{n-1}) of this cell's previous step
-        const bool hist = !eval_mode && a->hist_in;
         const int ws = (!eval_mode && !hist && T_.mlp) ? T_.ws_mode : 0;
         if (hist) {
             const T* Hc = a->hist_in + so;
@@ -1067,9 +1081,20 @@ struct CellSolver {
         const T kap = T_.kappa;
         T* x = a->x + so;
         T* v = a->v + so;
+        // compensated positions (see begin): x_{n+1} = x + (residue + u) as an FP32 value and
+        // its exact rounding error (two-sum, Knuth), which the next step adds back
+        T* XLO = a->hist_out && a->pos_stride > 0 ? a->hist_out + a->pos_stride + so : nullptr;
+        T* XHI = XLO ? XLO + a->pos_stride : nullptr;
+        const bool lo_in = XLO && a->hist_in;
         for (int i = tid; i < n; i += NT) {
             if (nonfinite) {
-                for (int c = 0; c < 3; ++c) v[c * n + i] = T(0);
+                for (int c = 0; c < 3; ++c) {
+                    v[c * n + i] = T(0);
+                    if (XLO) {
+                        XLO[c * n + i] = T(0);
+                        XHI[c * n + i] = x[c * n + i];
+                    }
+                }
                 continue;
             }
             T r[3];
@@ -1079,7 +1104,18 @@ struct CellSolver {
                 const T uc = u[c * np + i];
                 const T vv = uc * inv_h;
                 v[c * n + i] = vv + kap * (vc[c] + wr[c] - vv);
-                x[c * n + i] = x[c * n + i] + uc;
+                const T xo = x[c * n + i];
+                if (XLO) {
+                    const T t = (lo_in && XHI[c * n + i] == xo ? XLO[c * n + i] : T(0)) + uc;
+                    const T sm = xo + t;
+                    const T bv = sm - xo;
+                    const T err = (xo - (sm - bv)) + (t - bv);
+                    x[c * n + i] = sm;
+                    XLO[c * n + i] = err;
+                    XHI[c * n + i] = sm;
+                } else {
+                    x[c * n + i] = xo + uc;
+                }
             }
         }
         if (a->hist_out) {
