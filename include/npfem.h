@@ -163,7 +163,10 @@ int npfem_destroy(npfem_handle* h);
    groups (NPFEM_PREC_BF16 with every mesh of at most 960 vertices: one cluster launch
    per group, plus a SIMT launch on SMs the clusters leave idle, forked from and
    joined back to `stream`), preceded by the warm-start launch when a network is
-   installed.
+   installed.  With the temporal warm start (opts.warm_history) a cluster group's
+   launch is preceded by a SIMT launch over its cells that evaluates each at its first
+   iterate and finishes those already within the tolerance; the cluster launch then
+   solves only the others.
    meshes[g] and cells_per_group[g] (host arrays) name each group; all handles must
    share device, precision and dt.
    x, v: device SoA state (float, or double for NPFEM_PREC_FP64), updated in place
@@ -301,7 +304,7 @@ int npfem_get_tuning(const npfem_handle* h, int* use_tc, int* threads, int* fill
 
 /* A CUDA graph of `steps` consecutive npfem_step calls on fixed state buffers (the
    batching pattern of a time loop: the whole step, warm start and solver launches
-   included, replays as one graph launch).  Creation runs one step on temporary copies
+   included, replays as one graph launch).  Creation runs two steps on temporary copies
    of x and v (sizing the handles' buffers; x, v are not modified, stats is written)
    and captures the steps on an internal stream.  The graph holds the pointers it was
    created with; it must be destroyed before the handles.  Errors: INVALID_ARG, CUDA,

@@ -233,7 +233,8 @@ template <typename T>
 int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T* x, T* v, const T* f, const T* y,
               T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream,
               const T* u0 = nullptr, const long long* state_offs = nullptr, const long long* stats_offs = nullptr,
-              int threads = 0, const T* hist_in = nullptr, T* hist_out = nullptr, long long pos_stride = 0)
+              int threads = 0, const T* hist_in = nullptr, T* hist_out = nullptr, long long pos_stride = 0,
+              unsigned int* defer = nullptr)
 {
     npfem_handle* h0 = meshes[0];
     LaunchArgs<T> a;
@@ -274,6 +275,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     a.hist_in = hist_in;
     a.hist_out = hist_out;
     a.pos_stride = sizeof(T) == 4 && hist_out ? pos_stride : 0;
+    a.defer = defer;
 
     if (threads <= 0) threads = h0->threads;
     if (sizeof(T) == 8) threads = std::min(threads, 512);
@@ -304,7 +306,8 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
 
 // One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
 int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
-                 cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out, long long pos_stride)
+                 cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out, long long pos_stride,
+                 const unsigned int* only)
 {
     if (cells == 0) return 0;
     LaunchArgs<float> a;
@@ -313,6 +316,7 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     a.hist_in = hist_in;
     a.hist_out = hist_out;
     a.pos_stride = hist_out ? pos_stride : 0;
+    a.only = only;
     GroupDesc<float>& g = a.g[0];
     g.topo = h->tf;
     g.cell_begin = 0;
@@ -435,10 +439,39 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
             continue;
         }
         if (prec == NPFEM_PREC_BF16 && meshes[g]->n <= kTcMaxVerts && meshes[g]->use_tc) {
-            int rc = run_cells_tc(meshes[g], cells_per_group[g], (float*)x + soff[g], (float*)v + soff[g],
-                                  (const float*)f_ext + soff[g], stats ? stats + coff[g] : nullptr, s,
-                                  u0 ? u0 + soff[g] : nullptr, hist_in ? (const float*)hist_in + soff[g] : nullptr,
-                                  hist_out ? (float*)hist_out + soff[g] : nullptr, pos_stride);
+            npfem_handle* hg = meshes[g];
+            int32_t cg = cells_per_group[g];
+            float* xg = (float*)x + soff[g];
+            float* vg = (float*)v + soff[g];
+            const float* fg = (const float*)f_ext + soff[g];
+            npfem_cell_stats* sg = stats ? stats + coff[g] : nullptr;
+            const float* hin = hist_in ? (const float*)hist_in + soff[g] : nullptr;
+            float* hout = hist_out ? (float*)hist_out + soff[g] : nullptr;
+            const unsigned int* only = nullptr;
+            if (hout && (size_t)cg + 1 > hg->defer_len) {
+                // allocated with the history (first call of a trajectory), so that the
+                // steps that use it allocate nothing (they may be captured in a graph)
+                if (hg->defer) {
+                    NPFEM_CUDA(cudaStreamSynchronize(s));
+                    cudaFree(hg->defer);
+                    hg->defer = nullptr;
+                    hg->defer_len = 0;
+                }
+                NPFEM_CUDA(cudaMalloc(&hg->defer, sizeof(unsigned int) * ((size_t)cg + 1)));
+                hg->defer_len = (size_t)cg + 1;
+            }
+            if (hin && (size_t)cg + 1 <= hg->defer_len) {
+                // along a trajectory most cells are accepted at the first iterate: a SIMT
+                // launch on every SM evaluates each cell there and finishes those, and the
+                // cluster kernel takes only the rest (in lockstep rounds, cells without
+                // iterations would hold up the blocks that need a contraction)
+                NPFEM_CUDA(cudaMemsetAsync(hg->defer, 0, sizeof(unsigned int), s));
+                int rc = run_cells<float>(&hg, 1, &cg, xg, vg, fg, nullptr, nullptr, nullptr, sg, 0, s, nullptr,
+                                          nullptr, nullptr, 512, hin, hout, pos_stride, hg->defer);
+                if (rc) return rc;
+                only = hg->defer;
+            }
+            int rc = run_cells_tc(hg, cg, xg, vg, fg, sg, s, u0 ? u0 + soff[g] : nullptr, hin, hout, pos_stride, only);
             if (rc) return rc;
             done[g] = 1;
         }

@@ -128,6 +128,11 @@ struct LaunchArgs {
     // x_n + u below FP32 precision, sits at hist_out + pos_stride and the FP32 value it
     // belongs to at hist_out + 2 pos_stride; hist_in != null marks both as this trajectory's
     long long pos_stride;
+    // first-iterate pass (SIMT launch): cells not accepted at x^(1) are appended to
+    // defer ([0] count, then cell indices) and left untouched; the launch that follows
+    // takes only the cells listed in `only` (same layout; the count read on the device)
+    unsigned int* defer;
+    const unsigned int* only;
     double* parts;     // eval mode: 8 doubles per cell
     npfem_cell_stats* stats;
     char* scratch;     // per-CTA global slots for vectors that do not fit in smem
@@ -267,11 +272,15 @@ struct npfem_handle {
     size_t scratch_bytes = 0;
     float* ws_u = nullptr;  // learned first increments of the cluster kernel's cells
     size_t ws_u_len = 0;
-    // temporal warm start: corrections of the last step (element type of the state),
-    // valid for the groups and cell counts recorded in hist_sig
+    // temporal warm start: corrections of the last step (element type of the state) and,
+    // for FP32, the positions' rounding residues with their FP32 values; valid for the
+    // groups and cell counts recorded in hist_sig
     void* hist = nullptr;
     size_t hist_bytes = 0;
     std::vector<long long> hist_sig;
+    // cells the first-iterate pass leaves to the cluster kernel ([0] count, then indices)
+    unsigned int* defer = nullptr;
+    size_t defer_len = 0;
     int sm_count = 0, smem_optin = 0;
     int threads = 512;  // SIMT block size (512 or 640 for FP32 state)
     int use_tc = 1;     // BF16: use the tensor-core cluster kernel when the mesh fits it
@@ -319,6 +328,9 @@ struct npfem_handle {
         hist = nullptr;
         hist_bytes = 0;
         hist_sig.clear();
+        if (defer) cudaFree(defer);
+        defer = nullptr;
+        defer_len = 0;
         if (hx) cudaFree(hx);
         if (hv) cudaFree(hv);
         if (hf) cudaFree(hf);

@@ -674,7 +674,7 @@ struct CellSolver {
             }
             __syncthreads();
         }
-        evals = 1;
+        evals = a->only ? 2 : 1;  // a listed cell was evaluated once by the first-iterate pass
         if (ws == 2) {
             // keep the learned guess only if it lowers g: evaluate at y (trial buffers) first
             for (int e = tid; e < N3; e += NT) ut[e] = UYv[e];
@@ -1147,21 +1147,24 @@ __device__ __forceinline__ long long next_item(const LaunchArgs<T>& a, unsigned 
     CellShared<T>* sh = cell_shared<T>(smem);
     if (threadIdx.x == 0) {
         unsigned long long* cw = reinterpret_cast<unsigned long long*>(a.work);
+        // a launch over listed cells reads their number, written by an earlier launch
+        const long long total = a.only ? (long long)*reinterpret_cast<const volatile unsigned int*>(a.only) : a.total_cells;
         long long item = -1;
         if (a.claim_top) {
             // a slower helper: leaves the last `reserve` cells to the main launch
             const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(cw);
-            const long long left = a.total_cells - (long long)(cur & 0xffffffffull) - (long long)(cur >> 32);
+            const long long left = total - (long long)(cur & 0xffffffffull) - (long long)(cur >> 32);
             if (left > a.reserve) {
                 const unsigned long long old = atomicAdd(cw, 1ull << 32);
                 const long long lo = (long long)(old & 0xffffffffull), hi = (long long)(old >> 32);
-                if (lo + hi < a.total_cells) item = a.total_cells - 1 - hi;
+                if (lo + hi < total) item = total - 1 - hi;
             }
         } else {
             const unsigned long long old = atomicAdd(cw, 1ull);
             const long long lo = (long long)(old & 0xffffffffull), hi = (long long)(old >> 32);
-            if (lo + hi < a.total_cells) item = lo;
+            if (lo + hi < total) item = lo;
         }
+        if (item >= 0 && a.only) item = (long long)a.only[1 + item];
         sh->item = item;
     }
     __syncthreads();
@@ -1197,6 +1200,15 @@ __global__ void __launch_bounds__(MAXT, 1) cell_kernel(const __grid_constant__ L
         while (gi + 1 < a.n_groups && item >= a.g[gi + 1].cell_begin) ++gi;
         S.bind(a, a.g[gi], smem);
         if (!S.begin(item - a.g[gi].cell_begin, a.g[gi].stats_off + item - a.g[gi].cell_begin)) continue;
+        if (a.defer && S.wants_direction()) {
+            // first-iterate pass: the cell needs iterations, the launch that follows
+            // solves it from the unchanged state
+            if (threadIdx.x == 0) {
+                const unsigned int k = atomicAdd(a.defer, 1u);
+                a.defer[1 + k] = (unsigned int)item;
+            }
+            continue;
+        }
         const TopoDev<T>& tp = a.g[gi].topo;
         while (S.wants_direction()) {
             S.first_loop();

@@ -353,7 +353,9 @@ def test_bf16_idle_sm_fill_matches_clusters_only(npfem):
         h.check_device()
         assert (sg["status"] == 0).all() and (sg["residual"] <= 1e-6).all()
     assert max_rel_disp(out[0][0], out[1][0], m.lbar) <= 2e-5
-    assert out[0][1] == 2 and out[1][1] >= 2  # clusters only: one launch per step
+    # clusters only: one launch on the first step; on the second (temporal warm start)
+    # the first-iterate pass and the clusters
+    assert out[0][1] == 3 and out[1][1] >= 3
     sample = [0, 137, 399]
     xo, _, _ = oracle_steps(m, p["x"][sample], p["v"][sample], p["f"][sample], steps=2, tol=1e-10, max_iter=200)
     assert max_rel_disp(out[1][0][sample], xo, m.lbar) <= 2e-5 + fp32_store_allowance(p["x"], m.lbar)
@@ -446,6 +448,11 @@ def test_compensated_positions(npfem, prec):
         s = st.cpu().numpy().view(npfem.CELL_STATS_DTYPE).reshape(8)
         assert (s["status"] == 0).all() and (s["residual"] <= 1e-6).all()
         its.append(s["iterations"].mean())
+        if prec == "bf16" and len(its) > 1:
+            # the first-iterate pass accepts with one evaluation; a cell it leaves to the
+            # clusters is evaluated there again at the same point (counted)
+            it, ev = s["iterations"], s["evaluations"]
+            assert (ev[it == 0] == 1).all() and (ev[it > 0] >= it[it > 0] + 2).all(), (it, ev)
     assert np.mean(its[-40:]) <= 1.0, its[-40:]
     if "compensated" not in _ORACLE:
         # 1e-8: two orders below the GPU's tolerance, which sets the bound below
