@@ -357,8 +357,9 @@ def main():
     e2e = None
     if not args.no_e2e:
         barrier(pg)
-        ke = max(5, args.steps // 4)
-        e_s, bi, bo = e2e_leg(N, W, handle, pop, cells, ke, 2, torch)
+        # the device leg's steps of the same trajectory from the same start
+        ke = args.steps
+        e_s, bi, bo = e2e_leg(N, W, handle, pop, cells, ke, args.warmup, torch)
         e_s = max_over_ranks(pg, e_s)
         e2e = {"value": total_cells * ke / e_s, "unit": "RBC-steps/s", "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "steps": ke}

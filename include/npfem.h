@@ -166,7 +166,8 @@ int npfem_destroy(npfem_handle* h);
    installed.  With the temporal warm start (opts.warm_history) a cluster group's
    launch is preceded by a SIMT launch over its cells that evaluates each at its first
    iterate and finishes those already within the tolerance; the cluster launch then
-   solves only the others.
+   solves only the others.  While more than half of a group's cells needed iterations
+   in its previous step, that launch only lists the cells (no evaluation).
    meshes[g] and cells_per_group[g] (host arrays) name each group; all handles must
    share device, precision and dt.
    x, v: device SoA state (float, or double for NPFEM_PREC_FP64), updated in place

@@ -307,7 +307,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
 // One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
 int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
                  cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out, long long pos_stride,
-                 const unsigned int* only)
+                 unsigned int* only)
 {
     if (cells == 0) return 0;
     LaunchArgs<float> a;
@@ -317,6 +317,7 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     a.hist_out = hist_out;
     a.pos_stride = hist_out ? pos_stride : 0;
     a.only = only;
+    a.need = only ? only + 1 : nullptr;
     GroupDesc<float>& g = a.g[0];
     g.topo = h->tf;
     g.cell_begin = 0;
@@ -447,8 +448,8 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
             npfem_cell_stats* sg = stats ? stats + coff[g] : nullptr;
             const float* hin = hist_in ? (const float*)hist_in + soff[g] : nullptr;
             float* hout = hist_out ? (float*)hist_out + soff[g] : nullptr;
-            const unsigned int* only = nullptr;
-            if (hout && (size_t)cg + 1 > hg->defer_len) {
+            unsigned int* only = nullptr;
+            if (hout && (size_t)cg + 3 > hg->defer_len) {
                 // allocated with the history (first call of a trajectory), so that the
                 // steps that use it allocate nothing (they may be captured in a graph)
                 if (hg->defer) {
@@ -457,15 +458,17 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
                     hg->defer = nullptr;
                     hg->defer_len = 0;
                 }
-                NPFEM_CUDA(cudaMalloc(&hg->defer, sizeof(unsigned int) * ((size_t)cg + 1)));
-                hg->defer_len = (size_t)cg + 1;
+                NPFEM_CUDA(cudaMalloc(&hg->defer, sizeof(unsigned int) * ((size_t)cg + 3)));
+                hg->defer_len = (size_t)cg + 3;
+                NPFEM_CUDA(cudaMemsetAsync(hg->defer, 0, 3 * sizeof(unsigned int), s));
             }
-            if (hin && (size_t)cg + 1 <= hg->defer_len) {
+            if (hin && (size_t)cg + 3 <= hg->defer_len) {
                 // along a trajectory most cells are accepted at the first iterate: a SIMT
                 // launch on every SM evaluates each cell there and finishes those, and the
                 // cluster kernel takes only the rest (in lockstep rounds, cells without
                 // iterations would hold up the blocks that need a contraction)
-                NPFEM_CUDA(cudaMemsetAsync(hg->defer, 0, sizeof(unsigned int), s));
+                NPFEM_CUDA(cudaMemcpyAsync(hg->defer + 2, hg->defer + 1, sizeof(unsigned int), cudaMemcpyDeviceToDevice, s));
+                NPFEM_CUDA(cudaMemsetAsync(hg->defer, 0, 2 * sizeof(unsigned int), s));
                 int rc = run_cells<float>(&hg, 1, &cg, xg, vg, fg, nullptr, nullptr, nullptr, sg, 0, s, nullptr,
                                           nullptr, nullptr, 512, hin, hout, pos_stride, hg->defer);
                 if (rc) return rc;

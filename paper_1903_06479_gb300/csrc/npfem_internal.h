@@ -129,10 +129,15 @@ struct LaunchArgs {
     // belongs to at hist_out + 2 pos_stride; hist_in != null marks both as this trajectory's
     long long pos_stride;
     // first-iterate pass (SIMT launch): cells not accepted at x^(1) are appended to
-    // defer ([0] count, then cell indices) and left untouched; the launch that follows
-    // takes only the cells listed in `only` (same layout; the count read on the device)
+    // defer and left untouched.  Layout: [0] cells listed, [1] listed cells that
+    // needed iterations (counted by the launch that solves them), [2] that count of the
+    // previous step, then the cell indices.  When more than half of the cells needed
+    // iterations in the previous step, the pass lists every cell without evaluating.
+    // The launch that follows takes only the cells listed in `only` (the same buffer;
+    // the count read on the device) and counts into need[0]
     unsigned int* defer;
     const unsigned int* only;
+    unsigned int* need;
     double* parts;     // eval mode: 8 doubles per cell
     npfem_cell_stats* stats;
     char* scratch;     // per-CTA global slots for vectors that do not fit in smem
@@ -278,7 +283,8 @@ struct npfem_handle {
     void* hist = nullptr;
     size_t hist_bytes = 0;
     std::vector<long long> hist_sig;
-    // cells the first-iterate pass leaves to the cluster kernel ([0] count, then indices)
+    // cells the first-iterate pass leaves to the cluster kernel ([0] count, [1] cells
+    // that needed iterations, [2] the previous step's [1], then indices)
     unsigned int* defer = nullptr;
     size_t defer_len = 0;
     int sm_count = 0, smem_optin = 0;

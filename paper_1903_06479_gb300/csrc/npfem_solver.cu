@@ -674,7 +674,8 @@ struct CellSolver {
             }
             __syncthreads();
         }
-        evals = a->only ? 2 : 1;  // a listed cell was evaluated once by the first-iterate pass
+        // a listed cell was evaluated once by the first-iterate pass when that pass evaluated
+        evals = a->only && 2ll * (long long)a->only[2] <= a->total_cells ? 2 : 1;
         if (ws == 2) {
             // keep the learned guess only if it lowers g: evaluate at y (trial buffers) first
             for (int e = tid; e < N3; e += NT) ut[e] = UYv[e];
@@ -1164,7 +1165,7 @@ __device__ __forceinline__ long long next_item(const LaunchArgs<T>& a, unsigned 
             const long long lo = (long long)(old & 0xffffffffull), hi = (long long)(old >> 32);
             if (lo + hi < total) item = lo;
         }
-        if (item >= 0 && a.only) item = (long long)a.only[1 + item];
+        if (item >= 0 && a.only) item = (long long)a.only[3 + item];
         sh->item = item;
     }
     __syncthreads();
@@ -1193,20 +1194,25 @@ __global__ void __launch_bounds__(MAXT, 1) cell_kernel(const __grid_constant__ L
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     CellSolver<T> S;
+    // first-iterate pass: evaluate only while most cells of the last step were accepted
+    const bool eval_first = a.defer && 2ll * (long long)a.defer[2] <= a.total_cells;
     for (;;) {
         const long long item = next_item(a, smem);
         if (item < 0) break;
+        if (a.defer && !eval_first) {
+            if (threadIdx.x == 0) a.defer[3 + atomicAdd(a.defer, 1u)] = (unsigned int)item;
+            continue;
+        }
         int gi = 0;
         while (gi + 1 < a.n_groups && item >= a.g[gi + 1].cell_begin) ++gi;
         S.bind(a, a.g[gi], smem);
         if (!S.begin(item - a.g[gi].cell_begin, a.g[gi].stats_off + item - a.g[gi].cell_begin)) continue;
-        if (a.defer && S.wants_direction()) {
-            // first-iterate pass: the cell needs iterations, the launch that follows
-            // solves it from the unchanged state
-            if (threadIdx.x == 0) {
-                const unsigned int k = atomicAdd(a.defer, 1u);
-                a.defer[1 + k] = (unsigned int)item;
-            }
+        const bool wants = S.wants_direction();
+        if (a.need && wants && threadIdx.x == 0) atomicAdd(a.need, 1u);
+        if (a.defer && wants) {
+            // the cell needs iterations: the launch that follows solves it from the
+            // unchanged state
+            if (threadIdx.x == 0) a.defer[3 + atomicAdd(a.defer, 1u)] = (unsigned int)item;
             continue;
         }
         const TopoDev<T>& tp = a.g[gi].topo;
@@ -1457,6 +1463,8 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
                     break;
                 }
                 S.begin(item, item);
+                const bool wants = S.wants_direction();
+                if (a.need && wants && tid == 0) atomicAdd(a.need, 1u);
             } else if (have_result) {
                 have_result = false;
                 if ((phase == PH_DIR1 || phase == PH_FB1) && refine) {

@@ -443,16 +443,21 @@ def test_compensated_positions(npfem, prec):
     xs, vs, fs = (torch.tensor(W.to_soa(p[k]), dtype=torch.float32, device="cuda") for k in ("x", "v", "f"))
     st = torch.zeros((8, 32), dtype=torch.uint8, device="cuda")
     its = []
-    for _ in range(steps):
+    need = 0
+    for k in range(steps):
         npfem.step([h], [8], xs, vs, fs, h.dt, stats=st)
         s = st.cpu().numpy().view(npfem.CELL_STATS_DTYPE).reshape(8)
         assert (s["status"] == 0).all() and (s["residual"] <= 1e-6).all()
         its.append(s["iterations"].mean())
-        if prec == "bf16" and len(its) > 1:
-            # the first-iterate pass accepts with one evaluation; a cell it leaves to the
-            # clusters is evaluated there again at the same point (counted)
-            it, ev = s["iterations"], s["evaluations"]
-            assert (ev[it == 0] == 1).all() and (ev[it > 0] >= it[it > 0] + 2).all(), (it, ev)
+        it, ev = s["iterations"], s["evaluations"]
+        if prec == "bf16" and k >= 1 and (k == 1 or 2 * need <= 8):
+            # the first-iterate pass evaluated (at most half of the cells needed
+            # iterations in the step before): it accepts with one evaluation, and a cell
+            # it leaves to the clusters is evaluated there again at the same point
+            assert (ev[it == 0] == 1).all() and (ev[it > 0] >= it[it > 0] + 2).all(), (k, it, ev)
+        else:
+            assert (ev >= it + 1).all(), (k, it, ev)
+        need = int((it > 0).sum())
     assert np.mean(its[-40:]) <= 1.0, its[-40:]
     if "compensated" not in _ORACLE:
         # 1e-8: two orders below the GPU's tolerance, which sets the bound below
