@@ -66,7 +66,19 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--force-noise-regen", type=int, default=0,
+                    help="1: the N(0, 0.5 pN) force noise is redrawn every step (4 draws used in turn, copied in "
+                         "outside the step's events); 0: the force is fixed over the run")
     return ap.parse_args()
+
+
+FORCES_FIXED = "fixed over the run (shear traction at x_0 plus one N(0,0.5 pN) draw)"
+FORCES_REGEN = "shear traction at x_0 plus N(0,0.5 pN) noise redrawn every step (4 draws used in turn)"
+
+
+def workload_name(cells, regen):
+    return (f"{cells} RBCs x 642-vertex discocyte per GPU, shear traction U(10,1000)/s + N(0,0.5 pN), dt 0.1 us, "
+            f"tol 1e-6" + (", noise redrawn every step" if regen else ""))
 
 
 def dist_setup(n):
@@ -179,13 +191,13 @@ def peaks():
 # ----------------------------------------------------------------------------------
 # CPU oracle (reported baseline; also the reference arm)
 # ----------------------------------------------------------------------------------
-def oracle_sample(pop, cells, steps, threads):
+def oracle_sample(pop, cells, steps, threads, f=None):
     from oracle import oracle as O
     from paper_1903_06479_gb300 import workloads as W
     m = O.Model(pop["rest"], pop["tris"], W.material_vector(), DT)
     x = pop["x"][:cells].astype(np.float32).astype(np.float64)
     v = pop["v"][:cells].astype(np.float32).astype(np.float64)
-    f = pop["f"][:cells].astype(np.float32).astype(np.float64)
+    f = (pop["f"] if f is None else f)[:cells].astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
     m.step_batch(x, v, f, O.make_opts(tol=1e-6, max_iter=50), steps=steps, threads=threads)
     return time.perf_counter() - t0
@@ -200,18 +212,20 @@ def run_reference(args):
     pop = W.population(N_VERTS, cores, seed=1, forces="shear", noise_pN=0.5)
     from oracle import oracle as O
     O.build()
-    for _ in range(args.warmup):
-        oracle_sample(pop, cores, 1, cores)
+    fpool = W.noise_redrawn_forces(pop, cores, 7) if args.force_noise_regen else None
+    fk = lambda k: fpool[k % len(fpool)] if fpool else None
+    for k in range(args.warmup):
+        oracle_sample(pop, cores, 1, cores, fk(k))
     total = 0.0
-    for _ in range(args.steps):
-        total += oracle_sample(pop, cores, 1, cores)
+    for k in range(args.steps):
+        total += oracle_sample(pop, cores, 1, cores, fk(args.warmup + k))
     value = cores * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RBC-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.cells} RBCs x 642-vertex discocyte per GPU, shear traction U(10,1000)/s "
-                                   f"+ N(0,0.5 pN), dt 0.1 us, tol 1e-6",
+            "config": {"workload": workload_name(args.cells, args.force_noise_regen),
                        "cells_per_gpu": args.cells, "precision": "FP64 (CPU oracle)",
+                       "forces": FORCES_REGEN if args.force_noise_regen else FORCES_FIXED,
                        "timed_sample": f"{cores} of the cells, one time step each per timed step"},
             "cpu_baseline": {"value": value, "unit": "RBC-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{cores} cells x 1 time step per timed step, {args.steps} steps"},
@@ -222,13 +236,17 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------
 # GPU legs
 # ----------------------------------------------------------------------------------
-def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_times=False, graph=False):
+def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_times=False, graph=False, fpool=None):
     xs = torch.tensor(W.to_soa(pop["x"][:cells]), dtype=torch.float32, device="cuda")
     vs = torch.tensor(W.to_soa(pop["v"][:cells]), dtype=torch.float32, device="cuda")
     fs = torch.tensor(W.to_soa(pop["f"][:cells]), dtype=torch.float32, device="cuda")
     st = torch.zeros((cells, 32), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(warmup):
+    # forces redrawn every step: device copies of the draws, copied into fs before a step
+    fdev = [torch.tensor(W.to_soa(a), dtype=torch.float32, device="cuda") for a in fpool] if fpool else None
+    for k in range(warmup):
+        if fdev:
+            fs.copy_(fdev[k % len(fdev)])
         N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
     torch.cuda.synchronize()
     if kernel_times:
@@ -239,6 +257,8 @@ def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_tim
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = N.launch_count()
     for k in range(steps):
+        if fdev:
+            fs.copy_(fdev[(warmup + k) % len(fdev)])
         flush.zero_()  # writes a buffer larger than L2 between timed steps
         ev[k][0].record(stream)
         if g is not None:
@@ -265,19 +285,23 @@ def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_tim
             "kernel_ms": ktimes}
 
 
-def e2e_leg(N, W, handle, pop, cells, steps, warmup, torch):
+def e2e_leg(N, W, handle, pop, cells, steps, warmup, torch, fpool=None):
     x = torch.tensor(W.to_soa(pop["x"][:cells]), dtype=torch.float32).pin_memory()
     v = torch.tensor(W.to_soa(pop["v"][:cells]), dtype=torch.float32).pin_memory()
-    f = torch.tensor(W.to_soa(pop["f"][:cells]), dtype=torch.float32).pin_memory()
     stats = torch.zeros((cells, 32), dtype=torch.uint8).pin_memory()
-    xa, va, fa, sa = x.numpy(), v.numpy(), f.numpy(), stats.numpy()
+    xa, va, sa = x.numpy(), v.numpy(), stats.numpy()
+    # the step's force comes from pinned host memory: one array, or the redrawn draws in turn
+    fh = [torch.tensor(W.to_soa(a[:cells]), dtype=torch.float32).pin_memory() for a in (fpool or [pop["f"]])]
+    fa = [t.numpy() for t in fh]
     stream = torch.cuda.current_stream()
-    for _ in range(warmup):
-        handle.step_host(xa, va, fa, sa.view(N.CELL_STATS_DTYPE).reshape(cells), stream=stream.cuda_stream)
+    for k in range(warmup):
+        handle.step_host(xa, va, fa[k % len(fa)], sa.view(N.CELL_STATS_DTYPE).reshape(cells),
+                         stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        handle.step_host(xa, va, fa, sa.view(N.CELL_STATS_DTYPE).reshape(cells), stream=stream.cuda_stream)
+    for k in range(steps):
+        handle.step_host(xa, va, fa[(warmup + k) % len(fa)], sa.view(N.CELL_STATS_DTYPE).reshape(cells),
+                         stream=stream.cuda_stream)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     nb = 4 * 3 * N_VERTS * cells
@@ -312,6 +336,7 @@ def main():
     opts = N.default_opts(precision=args.precision, tol=1e-6, max_iter=50, refine=0, warm_history=args.history)
     handle = N.Handle(pop["rest"], pop["tris"], N.material(), opts, dt=DT, device=local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fpool = W.noise_redrawn_forces(pop, cells, 7 + rank) if args.force_noise_regen else None
 
     ws = None
     if args.warmstart == "learned" and args.precision != "fp64":
@@ -332,7 +357,7 @@ def main():
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
         dl = device_leg(N, W, handle, pop, cells, args.steps, args.warmup, torch, flush, kernel_times=True,
-                        graph=bool(args.graph))
+                        graph=bool(args.graph), fpool=fpool)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     barrier(pg)
@@ -347,7 +372,7 @@ def main():
     if not args.no_plain and (args.precision != "fp32" or ws is not None):
         hp = N.Handle(pop["rest"], pop["tris"], N.material(),
                       N.default_opts(precision="fp32", tol=1e-6, max_iter=50, warm_history=0), dt=DT, device=local)
-        pl = device_leg(N, W, hp, pop, cells, args.steps, args.warmup, torch, flush)
+        pl = device_leg(N, W, hp, pop, cells, args.steps, args.warmup, torch, flush, fpool=fpool)
         plain = {"value": total_cells * args.steps / max_over_ranks(pg, sum(pl["times"]) / 1e3),
                  "unit": "RBC-steps/s", "form": "FP32 SIMT contraction, first guess y", "steps": args.steps,
                  "iterations_per_cell": pl["iters"] / cells, "evaluations_per_cell": pl["evals"] / cells,
@@ -359,7 +384,7 @@ def main():
         barrier(pg)
         # the device leg's steps of the same trajectory from the same start
         ke = args.steps
-        e_s, bi, bo = e2e_leg(N, W, handle, pop, cells, ke, args.warmup, torch)
+        e_s, bi, bo = e2e_leg(N, W, handle, pop, cells, ke, args.warmup, torch, fpool=fpool)
         e_s = max_over_ranks(pg, e_s)
         e2e = {"value": total_cells * ke / e_s, "unit": "RBC-steps/s", "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "steps": ke}
@@ -388,7 +413,8 @@ def main():
         t = oracle_sample(pop, sample_cells, 10, cores)
         t1 = oracle_sample(pop, 8, 5, 1)
         cpu = {"value": sample_cells * 10 / t, "unit": "RBC-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{sample_cells} cells x 10 time steps of the same workload, FP64, {cores} threads",
+               "sample": f"{sample_cells} cells x 10 time steps of the same workload, FP64, {cores} threads"
+                         + (" (force fixed over the sample)" if args.force_noise_regen else ""),
                "value_1core": 8 * 5 / t1, "sample_1core": "8 cells x 5 time steps, 1 thread"}
 
     if rank == 0:
@@ -398,9 +424,9 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic",
-                "config": {"workload": f"{cells} RBCs x 642-vertex discocyte per GPU, shear traction U(10,1000)/s "
-                                       f"+ N(0,0.5 pN), dt 0.1 us, tol 1e-6",
+                "config": {"workload": workload_name(cells, args.force_noise_regen),
                            "cells_per_gpu": cells, "precision": prec_name,
+                           "forces": FORCES_REGEN if args.force_noise_regen else FORCES_FIXED,
                            "warm_start": ("learned MLP" if ws is not None else "first guess y")
                            + (" (first step), then previous step's correction" if args.history else ""),
                            "lbfgs_m": m,

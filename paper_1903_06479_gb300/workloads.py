@@ -159,7 +159,8 @@ def shear_forces(x: np.ndarray, tris: np.ndarray, gamma_dot_per_s: np.ndarray) -
 def population(n_verts: int, cells: int, seed: int, forces: str = "shear", noise_pN: float = 0.5,
                gamma_range=(10.0, 1000.0), gamma_fixed: float | None = None, box: float = 100.0,
                rotate: bool = True):
-    """A seeded population: returns dict(rest, tris, x [cells, n, 3], v, f), all float64.
+    """A seeded population: returns dict(rest, tris, x [cells, n, 3], v, f), all float64,
+    and for "shear" also f_shear, the traction without the noise.
 
     forces: "noise" (i.i.d. N(0, noise_pN)) or "shear" (traction of a linear shear flow at
     rate U(gamma_range) per cell, or gamma_fixed, plus N(0, noise_pN) noise)."""
@@ -167,14 +168,25 @@ def population(n_verts: int, cells: int, seed: int, forces: str = "shear", noise
     rest, tris = discocyte(n_verts)
     x = place_cells(rest, rng, cells, box=box, rotate=rotate)
     v = np.zeros_like(x)
+    out = dict(rest=rest, tris=tris, x=x, v=v)
     if forces == "noise":
-        f = rng.normal(0.0, noise_pN, size=x.shape)
+        out["f"] = rng.normal(0.0, noise_pN, size=x.shape)
     elif forces == "shear":
         g = np.full(cells, gamma_fixed) if gamma_fixed is not None else rng.uniform(*gamma_range, size=cells)
-        f = shear_forces(x, tris, g) + rng.normal(0.0, noise_pN, size=x.shape)
+        out["f_shear"] = shear_forces(x, tris, g)
+        out["f"] = out["f_shear"] + rng.normal(0.0, noise_pN, size=x.shape)
     else:
         raise ValueError(forces)
-    return dict(rest=rest, tris=tris, x=x, v=v, f=f)
+    return out
+
+
+def noise_redrawn_forces(pop: dict, cells: int, seed: int, draws: int = 4, noise_pN: float = 0.5) -> list:
+    """Force fields for a run whose noise is redrawn every step: the shear traction of
+    the population's first `cells` cells plus `draws` independent N(0, noise_pN) draws,
+    used in turn (step k takes draw k mod draws)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = pop["f_shear"][:cells]
+    return [base + rng.normal(0.0, noise_pN, size=base.shape) for _ in range(draws)]
 
 
 def material_vector(**overrides) -> np.ndarray:
