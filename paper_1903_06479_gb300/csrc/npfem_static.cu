@@ -18,8 +18,8 @@
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <string>
+#include <vector>
 
 #include "npfem_internal.h"
 
@@ -29,10 +29,6 @@
 static __device__ __align__(256) unsigned char g_npfem_static_scratch[NPFEM_STATIC_SCRATCH_BYTES];
 
 namespace {
-
-constexpr int kMaxDevices = 256;
-std::mutex g_static_mu;
-void* g_static_addr[kMaxDevices];  // device address of the array, per device
 
 struct CurrentDevice {
     int prev = -1;
@@ -49,48 +45,48 @@ struct CurrentDevice {
     }
 };
 
-// One-time set-up per device, run with that device current: look up the device
-// address of the array (a host-side reference to it is not a device pointer).
-int static_base(int device, char** out)
+// Device address of the array on the current device (a host-side reference to it is
+// not a device pointer).  Looked up on every call: the lookup allocates nothing, and
+// an address kept from an earlier context would be stale after a device reset.
+int static_base(char** out)
 {
-    if (device < 0 || device >= kMaxDevices) return npfem::set_error(NPFEM_ERR_INVALID_ARG, "device index out of range");
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_npfem_static_scratch);
-        if (e != cudaSuccess || !p)
-            return npfem::set_error(NPFEM_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch: ") +
-                                                        cudaGetErrorString(e));
-        g_static_addr[device] = p;
-    }
-    *out = static_cast<char*>(g_static_addr[device]);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_npfem_static_scratch);
+    if (e != cudaSuccess || !p)
+        return npfem::set_error(NPFEM_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch: ") +
+                                                    cudaGetErrorString(e));
+    *out = static_cast<char*>(p);
     return 0;
 }
 
+// One persistent SIMT launch over the groups `sel` (all of one block size), with the
+// groups' offsets into the caller's state and stats arrays.
 template <typename T>
-int run_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T* x, T* v, const T* f,
-               npfem_cell_stats* stats, char* base, cudaStream_t stream)
+int run_static(npfem_handle* const* meshes, const std::vector<int>& sel, const int32_t* cells,
+               const std::vector<long long>& soff, const std::vector<long long>& coff, int threads, T* x, T* v,
+               const T* f, npfem_cell_stats* stats, char* base, cudaStream_t stream)
 {
     using namespace npfem;
-    npfem_handle* h0 = meshes[0];
+    npfem_handle* h0 = meshes[sel[0]];
     LaunchArgs<T> a;
     memset(&a, 0, sizeof(a));
-    long long total = 0, state = 0, slot = 0;
+    long long total = 0, slot = 0;
     int smem_max = 0;
     const int budget = h0->smem_optin - kFixedSmem - 1024;
-    for (int gi = 0; gi < n_groups; ++gi) {
+    int ng = 0;
+    for (int gi : sel) {
         npfem_handle* h = meshes[gi];
-        GroupDesc<T>& g = a.g[gi];
+        GroupDesc<T>& g = a.g[ng++];
         g.topo = *reinterpret_cast<const TopoDev<T>*>(sizeof(T) == 4 ? (const void*)&h->tf : (const void*)&h->td);
         g.cell_begin = total;
-        g.state_off = state;
+        g.state_off = soff[gi];
+        g.stats_off = coff[gi];
         g.cells = cells[gi];
         long long sb = 0;
         place_vectors(&g, h->n_pad, h->nt, h0->opts.lbfgs_m, budget, &sb);
         slot = std::max(slot, sb);
         smem_max = std::max(smem_max, g.smem_bytes);
         total += cells[gi];
-        state += 3LL * h->n * cells[gi];
     }
     if (total == 0) return 0;
     const long long capacity = (long long)NPFEM_STATIC_SCRATCH_BYTES - NPFEM_STATIC_COUNTER_BYTES;
@@ -99,7 +95,7 @@ int run_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells, 
                          "npfem_step_static: one block needs " + std::to_string(slot) +
                              " bytes of scratch, more than the static array's " + std::to_string(capacity) +
                              " bytes (mesh too large for the allocation-free path)");
-    a.n_groups = n_groups;
+    a.n_groups = ng;
     a.total_cells = total;
     a.x = x;
     a.v = v;
@@ -113,13 +109,45 @@ int run_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells, 
     a.p.contraction = CONTRACT_SIMT;
 
     const int smem = kFixedSmem + smem_max;
-    const int per_sm = smem > h0->smem_optin / 2 ? 1 : (smem > h0->smem_optin / 3 ? 2 : 3);
+    cudaError_t e = set_cell_kernel_smem<T>(smem);
+    int per_sm = 1;
+    if (e == cudaSuccess) e = cells_per_sm<T>(threads, smem, &per_sm);
+    if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_step_static: ") + cudaGetErrorString(e));
+    per_sm = std::max(per_sm, 1);
     long long grid = std::min<long long>(total, (long long)h0->sm_count * per_sm);
     if (slot > 0) grid = std::min<long long>(grid, capacity / slot);  // fewer persistent blocks, same result
-    cudaError_t e = set_cell_kernel_smem<T>(smem);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, NPFEM_STATIC_COUNTER_BYTES, stream);
-    if (e == cudaSuccess) e = launch_cells<T>(a, (int)grid, h0->threads, smem, stream);
+    e = cudaMemsetAsync(base, 0, NPFEM_STATIC_COUNTER_BYTES, stream);
+    if (e == cudaSuccess) e = launch_cells<T>(a, (int)grid, threads, smem, stream);
     if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_step_static: ") + cudaGetErrorString(e));
+    return 0;
+}
+
+// The groups in launches of one block size each (the tuned SIMT block size of every
+// handle; 512 threads for FP64), in the order npfem_step launches its SIMT groups.
+template <typename T>
+int step_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T* x, T* v, const T* f,
+                npfem_cell_stats* stats, char* base, cudaStream_t stream)
+{
+    std::vector<long long> soff(n_groups), coff(n_groups);
+    long long st = 0, ct = 0;
+    for (int g = 0; g < n_groups; ++g) {
+        soff[g] = st;
+        coff[g] = ct;
+        st += 3LL * meshes[g]->n * cells[g];
+        ct += cells[g];
+    }
+    std::vector<char> done(n_groups, 0);
+    for (int g0 = 0; g0 < n_groups; ++g0) {
+        if (done[g0]) continue;
+        const int threads = sizeof(T) == 8 ? 512 : meshes[g0]->threads;
+        std::vector<int> sel;
+        for (int g = g0; g < n_groups; ++g) {
+            if (done[g] || (sizeof(T) == 4 && meshes[g]->threads != threads)) continue;
+            sel.push_back(g);
+            done[g] = 1;
+        }
+        if (int rc = run_static<T>(meshes, sel, cells, soff, coff, threads, x, v, f, stats, base, stream)) return rc;
+    }
     return 0;
 }
 
@@ -140,11 +168,11 @@ extern "C" int npfem_step_static(npfem_handle* const* meshes, int n_groups, cons
     if (dt != meshes[0]->dt) return npfem::set_error(NPFEM_ERR_INVALID_ARG, "dt differs from the handle's dt");
     CurrentDevice guard(meshes[0]->device);
     char* base = nullptr;
-    if (int rc = static_base(meshes[0]->device, &base)) return rc;
+    if (int rc = static_base(&base)) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (meshes[0]->precision == NPFEM_PREC_FP64)
-        return run_static<double>(meshes, n_groups, cells_per_group, (double*)x, (double*)v, (const double*)f_ext, stats,
-                                  base, s);
-    return run_static<float>(meshes, n_groups, cells_per_group, (float*)x, (float*)v, (const float*)f_ext, stats, base,
-                             s);
+        return step_static<double>(meshes, n_groups, cells_per_group, (double*)x, (double*)v, (const double*)f_ext,
+                                   stats, base, s);
+    return step_static<float>(meshes, n_groups, cells_per_group, (float*)x, (float*)v, (const float*)f_ext, stats, base,
+                              s);
 }
