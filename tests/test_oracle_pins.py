@@ -312,6 +312,99 @@ def test_first_guess_lumped(m642):
     assert np.abs(y - (x + DT * v + DT ** 2 * f / M)).max() < 1e-14
 
 
+def flat_vertex_configuration(model, i):
+    """Rest shape with vertex i moved to the cotangent-weighted centre of its one-ring,
+    where delta_f = sum_j c_ij (x_j - x_i) vanishes (the 1/(2 A_i) factor of c_ij is
+    common to the ring and drops out); also the current area-weighted normal there."""
+    x = model.rest.copy()
+    T = model.tris
+    wsum, acc = 0.0, np.zeros(3)
+    for t in T:
+        for a in range(3):
+            # the edge opposite corner a gets cot(angle at a) for both its ends
+            p, q, r = t[a], t[(a + 1) % 3], t[(a + 2) % 3]
+            u, v = x[q] - x[p], x[r] - x[p]
+            cot = np.dot(u, v) / np.linalg.norm(np.cross(u, v))
+            if q == i:
+                wsum += cot; acc += cot * x[r]
+            elif r == i:
+                wsum += cot; acc += cot * x[q]
+    x[i] = acc / wsum
+    nrm = np.zeros(3)
+    for t in T:
+        if i in t:
+            nrm += 0.5 * np.cross(x[t[1]] - x[t[0]], x[t[2]] - x[t[0]])
+    return x, nrm / np.linalg.norm(nrm)
+
+
+def test_bending_flat_vertex_branch():
+    # Bending (Sec. 2.1.2): at delta_f = 0 the closest point on the sphere {R delta_g} is
+    # not unique; the reading takes it along the current vertex normal, oriented as
+    # delta_g is to the rest normal (inward on the convex rim).  Moving the vertex
+    # outward by eps keeps that projection (delta_f = eps csum n points inward), so
+    # g along the ray is smooth for eps >= 0: the branch's energy must be the ray's
+    # limit at 0 and its gradient the one-sided derivative (a sign error flips it).
+    rest, tris = W.discocyte(258)
+    m = O.Model(rest, tris, W.material_vector(), DT)
+    i = int(np.argmax(np.hypot(rest[:, 0], rest[:, 1])))  # a rim vertex (convex)
+    x0, nhat = flat_vertex_configuration(m, i)
+    E = lambda e: m.energy_bend(np.where(np.arange(m.n)[:, None] == i, x0 + e * nhat, x0))[0]
+    E0, G0 = m.energy_bend(x0)
+    h = 1e-4 * m.lbar
+    E1, E2, E3 = E(h), E(2 * h), E(3 * h)
+    assert abs(E0 - (3 * E1 - 3 * E2 + E3)) <= 1e-9 * E0
+    d1 = (-3 * E0 + 4 * E1 - E2) / (2 * h)
+    assert abs(np.dot(G0[i], nhat) - d1) <= 1e-5 * np.abs(G0).max()
+    # the other side of the vertex is a different branch: the derivative differs
+    Em = lambda e: E(-e)
+    dm = (-3 * E0 + 4 * Em(h) - Em(2 * h)) / (2 * h)
+    assert abs(-np.dot(G0[i], nhat) - dm) > 1e-2 * np.abs(G0).max()
+
+
+def test_first_guess_rayleigh_beta():
+    # beta_D > 0 (Sec. 2.1.4, C = alpha_D M + beta_D L with the PD matrix L standing in
+    # for the stiffness): M~ = M + h C is not diagonal, and the first guess of
+    # Eq. preOptimizationNewton is the solution of M~ (y - x) = h M v + h^2 F_ext.
+    # M~ is formed here from the oracle's masses and L, the residual is dense.
+    rest, tris = W.discocyte(258)
+    beta, alpha = 0.01, 0.002
+    m = O.Model(rest, tris, W.material_vector(beta_D=beta, alpha_D=alpha), DT)
+    rng = np.random.default_rng(31)
+    x, v, f = rest.copy(), 0.01 * rng.standard_normal(rest.shape), 2.0 * rng.standard_normal(rest.shape)
+    y = m.first_guess(x, v, f)
+    Mv = m.masses()[:, None]
+    Mt = np.diag(m.masses() * (1 + DT * alpha)) + DT * beta * m.laplacian()
+    rhs = DT * Mv * v + DT ** 2 * f
+    assert np.abs(Mt @ (y - x) - rhs).max() <= 1e-12 * np.abs(rhs).max()
+    # the coupling is not negligible: y differs from the lumped first guess
+    y_lumped = x + rhs / (Mv * (1 + DT * alpha))
+    assert np.abs(y - y_lumped).max() > 1e-3 * np.abs(y_lumped - x).max()
+    # H~ = M~ / h^2 + L (Sec. 2.1.1)
+    assert np.abs(m.hessian() - (Mt / DT ** 2 + m.laplacian())).max() <= 1e-12 * np.abs(m.hessian()).max()
+
+
+def test_objective_gradient_rayleigh_beta_finite_differences():
+    # With beta_D > 0 the inertia term (1/2h^2)(x - y)^T M~ (x - y) couples vertices; its
+    # gradient M~ (x - y) / h^2 plus the exact energy gradients (no volume term, whose PD
+    # gradient is the linearised projection) must match central differences of g.
+    rest, tris = W.discocyte(66)
+    m = O.Model(rest, tris, W.material_vector(beta_D=0.02, k_vol=0.0), DT)
+    rng = np.random.default_rng(32)
+    x = rest + 0.02 * m.lbar * rng.standard_normal(rest.shape)
+    y = x + 0.01 * m.lbar * rng.standard_normal(rest.shape)
+    E, G, parts = m.objective(x, y)
+    Mt = np.diag(m.masses()) + DT * 0.02 * m.laplacian()
+    assert abs(parts[0] - 0.5 / DT ** 2 * np.sum((x - y) * (Mt @ (x - y)))) <= 1e-12 * parts[0]
+    h = 1e-6 * m.lbar
+    fd = np.zeros_like(x)
+    for i in range(m.n):
+        for c in range(3):
+            xp = x.copy(); xp[i, c] += h
+            xm = x.copy(); xm[i, c] -= h
+            fd[i, c] = (m.objective(xp, y)[0] - m.objective(xm, y)[0]) / (2 * h)
+    assert np.abs(fd - G).max() <= 1e-6 * np.abs(G).max()
+
+
 def test_rayleigh_modal_damping_ratio_small():
     # Reading of beta_D = 0.01 in microseconds: zeta = beta omega / 2 <= 0.1 for all
     # modes of L x = omega^2 M x (Sec. 2.1.4).
