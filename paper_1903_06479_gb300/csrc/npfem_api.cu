@@ -79,7 +79,7 @@ int upload(npfem_handle* h, const std::vector<S>& src, const X** out)
 }
 
 template <typename T>
-int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv)
+int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv, const void* minv)
 {
     const HostTopo& H = h->host;
     int rc;
@@ -186,6 +186,17 @@ int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv)
     tp->n_pad = h->n_pad;
     tp->nnz = (int)H.ring_idx.size();
     tp->ainv = static_cast<const T*>(ainv);
+    tp->minv = static_cast<const T*>(minv);
+    tp->l_ptr = nullptr;
+    tp->l_idx = nullptr;
+    tp->l_val = nullptr;
+    tp->beta_h = (T)(h->mat.beta_D / h->dt);
+    if (minv) {
+        if ((rc = upload(h, H.L_ptr, &tp->l_ptr))) return rc;
+        std::vector<unsigned short> lidx(H.L_idx.begin(), H.L_idx.end());
+        if ((rc = upload(h, lidx, &tp->l_idx))) return rc;
+        if ((rc = upload(h, H.L_val, &tp->l_val))) return rc;
+    }
     tp->ainv_lp = nullptr;
     tp->h_ptr = nullptr;
     tp->h_idx = nullptr;
@@ -729,10 +740,8 @@ int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_
     *out = nullptr;
     if (!(dt > 0.0) || !isfinite(dt)) return fail(NPFEM_ERR_INVALID_ARG, "dt must be positive");
     if (int rc = check_opts(opts)) return rc;
-    if (mat->beta_D != 0.0)
-        return fail(NPFEM_ERR_INVALID_ARG, "beta_D != 0 (stiffness-proportional Rayleigh damping) is not supported");
     if (!(mat->density > 0.0) || mat->kappa < 0.0 || mat->kappa > 1.0 || mat->C < 0 || mat->B < 0 || mat->D < 0 ||
-        mat->k_bend < 0 || mat->k_vol < 0 || mat->k_mat_hess < 0 || mat->alpha_D < 0)
+        mat->k_bend < 0 || mat->k_vol < 0 || mat->k_mat_hess < 0 || mat->alpha_D < 0 || !(mat->beta_D >= 0.0))
         return fail(NPFEM_ERR_INVALID_ARG, "material: need density > 0, kappa in [0,1], non-negative moduli");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -764,27 +773,65 @@ int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_
     };
     const int n = h->n, np = h->n_pad;
     int e = 0;
-    // dense H~ = M~/h^2 + L in FP64, inverted on the GPU
+    // dense H~ = M~/h^2 + L in FP64, inverted on the GPU.  Rayleigh damping
+    // C = alpha_D M + beta_D L (Sec. 2.1.4) gives M~ = (1 + h alpha_D) M + h beta_D L, so
+    // H~ = (1 + h alpha_D)/h^2 M + (1 + beta_D/h) L
     std::vector<double> H((size_t)n * n, 0.0);
     const double ms = (1.0 + dt * mat->alpha_D) / (dt * dt);
+    const double lscale = 1.0 + mat->beta_D / dt;
     for (int i = 0; i < n; ++i) {
         H[(size_t)i * n + i] += ms * h->host.mass[i];
-        for (int q = h->host.L_ptr[i]; q < h->host.L_ptr[i + 1]; ++q) H[(size_t)i * n + h->host.L_idx[q]] += h->host.L_val[q];
+        for (int q = h->host.L_ptr[i]; q < h->host.L_ptr[i + 1]; ++q)
+            H[(size_t)i * n + h->host.L_idx[q]] += lscale * h->host.L_val[q];
     }
     h->ainv64 = h->alloc<double>((size_t)n * n, &e);
-    double* col = h->alloc<double>(n, &e);
+    double* prow = h->alloc<double>(2 * (size_t)n, &e);
     int* flag = h->alloc<int>(4, &e);
     h->work = h->alloc<unsigned int>(4, &e);
     if (e) return bail(e);
-    if (cudaMemcpy(h->ainv64, H.data(), H.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(flag, 0, 4 * sizeof(int)) != cudaSuccess || cudaMemset(h->work, 0, 4 * sizeof(unsigned)) != cudaSuccess)
-        return bail(fail(NPFEM_ERR_CUDA, "upload of H~ failed"));
-    cudaError_t ce = invert_spd_fp64(h->ainv64, n, col, flag, 0);
-    if (ce != cudaSuccess) return bail(fail(NPFEM_ERR_CUDA, std::string("inversion: ") + cudaGetErrorString(ce)));
-    int hflag = 0;
-    if (cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return bail(fail(NPFEM_ERR_CUDA, "inversion failed"));
-    if (hflag) return bail(fail(NPFEM_ERR_NOT_SPD, "H~ is not positive definite"));
+    // one inversion on the GPU: the dense FP64 matrix in, its inverse in place
+    auto invert = [&](double* dA, const std::vector<double>& A, const char* what) -> int {
+        if (cudaMemcpy(dA, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(flag, 0, 4 * sizeof(int)) != cudaSuccess)
+            return fail(NPFEM_ERR_CUDA, std::string("upload of ") + what + " failed");
+        cudaError_t ce = invert_spd_fp64(dA, n, prow, flag, 0);
+        if (ce != cudaSuccess) return fail(NPFEM_ERR_CUDA, std::string("inversion of ") + what + ": " + cudaGetErrorString(ce));
+        int hflag = 0;
+        if (cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(NPFEM_ERR_CUDA, std::string("inversion of ") + what + " failed");
+        if (hflag == 2) return fail(NPFEM_ERR_TIMEOUT, std::string("inversion of ") + what + ": a grid barrier gave up");
+        if (hflag) return fail(NPFEM_ERR_NOT_SPD, std::string(what) + " is not positive definite");
+        return 0;
+    };
+    if (cudaMemset(h->work, 0, 4 * sizeof(unsigned)) != cudaSuccess) return bail(fail(NPFEM_ERR_CUDA, "memset failed"));
+    if ((rc = invert(h->ainv64, H, "H~"))) return bail(rc);
+    cudaError_t ce = cudaSuccess;
+    // beta_D > 0: M~ is not diagonal; the first guess applies M~^-1 (dense, inverted once
+    // like H~) and the inertia term needs h beta_D L (sparse, in the solver's type)
+    void* minv_t = nullptr;
+    if (mat->beta_D > 0.0) {
+        std::vector<double> Mt((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            Mt[(size_t)i * n + i] += (1.0 + dt * mat->alpha_D) * h->host.mass[i];
+            for (int q = h->host.L_ptr[i]; q < h->host.L_ptr[i + 1]; ++q)
+                Mt[(size_t)i * n + h->host.L_idx[q]] += dt * mat->beta_D * h->host.L_val[q];
+        }
+        double* m64 = h->alloc<double>((size_t)n * n, &e);
+        if (e) return bail(e);
+        if ((rc = invert(m64, Mt, "M~"))) return bail(rc);
+        if (h->precision == NPFEM_PREC_FP64) {
+            double* o = h->alloc<double>((size_t)np * np, &e);
+            if (e) return bail(e);
+            ce = publish_inverse(m64, n, np, nullptr, o, nullptr, nullptr, 0);
+            minv_t = o;
+        } else {
+            float* o = h->alloc<float>((size_t)np * np, &e);
+            if (e) return bail(e);
+            ce = publish_inverse(m64, n, np, o, nullptr, nullptr, nullptr, 0);
+            minv_t = o;
+        }
+        if (ce != cudaSuccess) return bail(fail(NPFEM_ERR_CUDA, "publishing M~^-1 failed"));
+    }
 
     void* ainv_t = nullptr;
     if (h->precision == NPFEM_PREC_FP64) {
@@ -800,7 +847,8 @@ int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_
     }
     if (ce != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
         return bail(fail(NPFEM_ERR_CUDA, "publishing A^-1 failed"));
-    rc = h->precision == NPFEM_PREC_FP64 ? fill_topo<double>(h, &h->td, ainv_t) : fill_topo<float>(h, &h->tf, ainv_t);
+    rc = h->precision == NPFEM_PREC_FP64 ? fill_topo<double>(h, &h->td, ainv_t, minv_t)
+                                         : fill_topo<float>(h, &h->tf, ainv_t, minv_t);
     if (rc) return bail(rc);
     if (h->precision == NPFEM_PREC_BF16) {
         // tensor-core path: BF16 A^-1 in 128-row blocks with K padded to 16, and L for
@@ -814,7 +862,9 @@ int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_
         h->tf.ainv_lp = abf;
         h->tf.kpad = kpad;
         h->tf.rb = rb;
-        std::vector<float> lval(h->host.L_val.begin(), h->host.L_val.end());
+        // the refinement residual q - H~ r needs H~ = ms M + (1 + beta_D/h) L
+        std::vector<float> lval(h->host.L_val.size());
+        for (size_t q = 0; q < lval.size(); ++q) lval[q] = (float)(lscale * h->host.L_val[q]);
         std::vector<unsigned short> lidx(h->host.L_idx.begin(), h->host.L_idx.end());
         if ((rc = upload(h, h->host.L_ptr, &h->tf.h_ptr))) return bail(rc);
         if ((rc = upload(h, lidx, &h->tf.h_idx))) return bail(rc);
@@ -991,6 +1041,16 @@ int npfem_check_device(npfem_handle* h)
         NPFEM_CUDA(cudaMemset(h->work + 2, 0, sizeof(unsigned)));
         return fail(NPFEM_ERR_TIMEOUT, "a bounded device wait gave up in a previous step (tensor-core MMA completion)");
     }
+    return 0;
+}
+
+int npfem_flag_wait_timeout(npfem_handle* h)
+{
+    if (!h) return fail(NPFEM_ERR_INVALID_ARG, "null handle");
+    DeviceGuard guard(h->device);
+    NPFEM_CUDA(cudaDeviceSynchronize());
+    const unsigned one = 1u;
+    NPFEM_CUDA(cudaMemcpy(h->work + 2, &one, sizeof(unsigned), cudaMemcpyHostToDevice));
     return 0;
 }
 

@@ -2,7 +2,7 @@
 // (Sec. 2.1.1: H~ is constant and SPD, so it is factored once).  The library keeps
 // the dense inverse A^-1 so that every cell sharing a topology applies it as a
 // contraction.  Gauss-Jordan elimination without pivoting is stable for SPD
-// matrices; each pivot step is two launches (pivot row, rank-1 update).
+// matrices; the whole elimination is one cooperative launch.
 #include <cuda_bf16.h>
 
 #include "npfem_internal.h"
@@ -10,35 +10,83 @@
 namespace npfem {
 namespace {
 
-// Scales pivot row k and saves column k (before the update) in col[].
-__global__ void gj_pivot_row(double* A, double* col, int n, int k, int* not_spd)
+// Grid-wide barrier of the cooperative inversion kernel (all blocks co-resident).
+// The wait is bounded: after kGjSpinLimit polls the block records flag 2 (reported
+// as a timeout by the host) and goes on, and every block stops waiting once the flag
+// is set, so the kernel always ends.
+constexpr unsigned kGjSpinLimit = 1u << 24;
+
+__device__ __forceinline__ void gj_grid_barrier(unsigned* bar, unsigned& gen, int* flag)
 {
-    double piv = A[(size_t)k * n + k];
-    if (!(piv > 0.0)) {
-        if (threadIdx.x == 0 && blockIdx.x == 0) *not_spd = 1;
-        piv = 1.0;  // keep going; the result is discarded by the host
-    }
-    double p = 1.0 / piv;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        col[i] = (i == k) ? 0.0 : A[(size_t)i * n + k];
-    }
-    // every block must have read column k before row k changes: single-block launch
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double a = (j == k) ? 1.0 : A[(size_t)k * n + j];
-        A[(size_t)k * n + j] = a * p;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicExch(bar + 1, gen + 1);
+        } else {
+            volatile int* vflag = flag;
+            unsigned it = 0;
+            while (*vgen == gen) {
+                if (++it > kGjSpinLimit) {
+                    atomicExch(flag, 2);
+                    break;
+                }
+                if (*vflag == 2) break;  // another block gave up: the result is discarded anyway
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
     }
+    ++gen;
+    __syncthreads();
 }
 
-// A[i][j] <- (j == k ? 0 : A[i][j]) - col[i] * A[k][j] for every row i != k.
-__global__ void gj_update(double* A, const double* col, int n, int k)
+// In-place Gauss-Jordan inversion of an SPD matrix in one cooperative launch: one
+// grid barrier per pivot.  Warps own rows (coalesced over columns).  Pivot step k
+// needs row k as it stands after step k-1 while its owner overwrites it, so that row
+// is read from a snapshot: the owner of row k+1 writes its updated row into
+// prow[(k+1) & 1] during step k, a buffer nobody reads in step k.  Per element the
+// arithmetic is the textbook one: the pivot row scaled by 1/a_kk, then
+// a_ij <- a_ij - a_ik a'_kj with a'_kk = 1/a_kk and a_ik replaced by 0.
+__global__ void __launch_bounds__(256) gj_invert_coop(double* A, double* prow, int n, unsigned* bar, int* flag)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
-    if (j >= n || i == k) return;
-    double f = col[i];
-    double a = (j == k) ? 0.0 : A[(size_t)i * n + j];
-    A[(size_t)i * n + j] = a - f * A[(size_t)k * n + j];
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    unsigned gen = 0;
+    if (gw == 0)
+        for (int j = lane; j < n; j += 32) prow[j] = __ldcg(A + j);
+    gj_grid_barrier(bar, gen, flag);
+    for (int k = 0; k < n; ++k) {
+        const double* pk = prow + (size_t)(k & 1) * n;
+        double* pn = prow + (size_t)((k + 1) & 1) * n;
+        double piv = __ldcg(pk + k);
+        if (!(piv > 0.0)) {
+            if (gw == 0 && lane == 0) atomicCAS(flag, 0, 1);
+            piv = 1.0;  // keep going; the host discards the result
+        }
+        const double p = 1.0 / piv;
+        for (int i = gw; i < n; i += nw) {
+            double* Ai = A + (size_t)i * n;
+            if (i == k) {
+                for (int j = lane; j < n; j += 32) Ai[j] = (j == k ? 1.0 : __ldcg(pk + j)) * p;
+                continue;
+            }
+            const double f = __ldcg(Ai + k);
+            __syncwarp();
+            for (int j = lane; j < n; j += 32) {
+                const double a = j == k ? 0.0 : __ldcg(Ai + j);
+                const double v = a - f * ((j == k ? 1.0 : __ldcg(pk + j)) * p);
+                Ai[j] = v;
+                if (i == k + 1) pn[j] = v;
+            }
+        }
+        gj_grid_barrier(bar, gen, flag);
+    }
 }
 
 // A <- (A + A^T)/2 in place; each (i < j) pair is owned by one thread.
@@ -95,14 +143,24 @@ cudaError_t publish_inverse_bf16_blocked(const double* A, int n, int rows_pad, i
     return cudaGetLastError();
 }
 
-cudaError_t invert_spd_fp64(double* A, int n, double* col, int* d_flag, cudaStream_t s)
+cudaError_t invert_spd_fp64(double* A, int n, double* prow, int* d_flag, cudaStream_t s)
 {
-    dim3 ub(256), ug((n + 255) / 256, n);
-    for (int k = 0; k < n; ++k) {
-        gj_pivot_row<<<1, 512, 0, s>>>(A, col, n, k, d_flag);
-        gj_update<<<ug, ub, 0, s>>>(A, col, n, k);
-        count_launch(2);
-    }
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_invert_coop, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (!coop || per_sm < 1) return cudaErrorNotSupported;
+    // one block per SM: every block is resident, so the grid barrier cannot wait on an
+    // unscheduled block; the barrier words sit behind the flag (d_flag[2], d_flag[3])
+    const int grid = sms;
+    unsigned* bar = reinterpret_cast<unsigned*>(d_flag + 2);
+    void* args[] = {&A, &prow, &n, &bar, &d_flag};
+    e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void*)gj_invert_coop, dim3(grid), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    count_launch();
     return cudaGetLastError();
 }
 

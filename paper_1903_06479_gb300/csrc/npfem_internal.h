@@ -58,6 +58,14 @@ struct TopoDev {
     const T* ring8_c;                 // [n][8]
     const T* ring8_ct;                // [n][8]
     const T* ainv;               // [n_pad][n_pad] A^-1 in T (zero padding)
+    // Rayleigh damping with beta_D > 0: M~ = (1 + h alpha_D) M + h beta_D L is not
+    // diagonal.  minv: [n_pad][n_pad] M~^-1 in T for the first guess; L (CSR, T) for the
+    // inertia term's h beta_D L part; beta_h = beta_D / h.  Null pointers when beta_D = 0.
+    const T* minv;
+    const int* l_ptr;
+    const unsigned short* l_idx;
+    const T* l_val;
+    T beta_h;
     const void* ainv_lp;         // A^-1 for the tensor-core contraction (bf16 or tf32-rounded fp32)
     const int* h_ptr;            // L (CSR, fp32) for the refinement residual q - H~ r
     const unsigned short* h_idx;
@@ -172,9 +180,11 @@ int build_host_topo(const npfem_mesh* mesh, const npfem_material* mat, int equal
                     std::string* err);
 
 // ---- kernels (npfem_factor.cu, npfem_solver.cu) ---------------------------------
-// In-place FP64 Gauss-Jordan inversion of an SPD n x n matrix on the GPU; sets
-// *not_spd when a pivot is not positive.
-cudaError_t invert_spd_fp64(double* A, int n, double* col_scratch, int* d_flag, cudaStream_t s);
+// In-place FP64 Gauss-Jordan inversion of an SPD n x n matrix on the GPU in one
+// cooperative launch.  prow: 2n doubles of scratch; d_flag: 4 ints, zeroed by the
+// caller: d_flag[0] becomes 1 when a pivot is not positive, 2 when a grid barrier
+// gave up waiting; d_flag[2..3] are the barrier's words.
+cudaError_t invert_spd_fp64(double* A, int n, double* prow, int* d_flag, cudaStream_t s);
 // Symmetrise A^-1 (FP64, n x n) and write padded copies in fp32 / fp64 / bf16.
 cudaError_t publish_inverse(const double* A, int n, int n_pad, float* out32, double* out64, void* out_bf16,
                             float* out_tf32, cudaStream_t s);

@@ -410,6 +410,10 @@ int npfem_set_warmstart(npfem_handle* h, const float* params_host, int mode)
         return set_error(NPFEM_ERR_INVALID_ARG, "npfem_set_warmstart: need a handle, mode 0..2 and parameters for mode > 0");
     if (h->precision == NPFEM_PREC_FP64)
         return set_error(NPFEM_ERR_INVALID_ARG, "npfem_set_warmstart: FP32 state handles only");
+    if (mode > 0 && h->mat.beta_D != 0.0)
+        return set_error(NPFEM_ERR_INVALID_ARG,
+                         "npfem_set_warmstart: the network's features use the lumped first guess; beta_D > 0 "
+                         "(non-diagonal M~) is not supported");
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != h->device) cudaSetDevice(h->device);

@@ -364,7 +364,7 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
     });
     const T volc = sh->volc;
 
-    // ---- pass 3: bending gather, volume and inertia (M~ = (1 + h alpha_D) M), residual
+    // ---- pass 3: bending gather, volume and inertia (M~ = (1 + h alpha_D) M + h beta_D L), residual
     const T ms = tp.inertia_scale * tp.inv_h2, h2 = tp.h * tp.h;
     Acc<T> ci[1];            // inertia energy
     T pr[1] = {T(0)};        // sum_i (h^2 |grad_i| / m_i)^2
@@ -395,13 +395,26 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
                 for (int c = 0; c < 3; ++c) gb[c] += ct * WR[c * np + jn];
             }
         }
+        // beta_D > 0: M~/h^2 (x - y) gains (beta_D / h) L (x - y)
+        T lb[3] = {T(0), T(0), T(0)};
+        if (tp.l_ptr) {
+            const int b0 = __ldg(&tp.l_ptr[i]), b1 = __ldg(&tp.l_ptr[i + 1]);
+            for (int q = b0; q < b1; ++q) {
+                const int j = __ldg(&tp.l_idx[q]);
+                const T lv = __ldg(&tp.l_val[q]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) lb[c] += lv * (U[c * np + j] - UY[c * np + j]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) lb[c] *= tp.beta_h;
+        }
         T g2 = T(0), ei = T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T du = U[c * np + i] - UY[c * np + i];
-            const T gv = Gout[c * np + i] + gb[c] + volc * GC[c * np + i] + m * ms * du;
+            const T gv = Gout[c * np + i] + gb[c] + volc * GC[c * np + i] + m * ms * du + lb[c];
             Gout[c * np + i] = gv;
-            ei += T(0.5) * m * ms * du * du;
+            ei += T(0.5) * (m * ms * du + lb[c]) * du;
             g2 += gv * gv;
         }
         ci[0].add(ei);
@@ -420,18 +433,19 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
     });
 }
 
-// R = A^-1 Q for the three coordinate rows.
+// R = A Q for the three coordinate rows, A = A^-1 of the topology unless another
+// symmetric matrix of the same padded layout is given (M~^-1 for the first guess).
 // FP32: a warp owns a tile of 128 rows (4 consecutive rows per lane, float4 loads of
 // the symmetric A^-1 by columns, coalesced) and a share of the j range; Q is
 // broadcast from shared memory.  The warps' partial sums go to `scratch` (the
 // triangle buffer, idle outside the objective evaluation) and are added in a fixed
 // order, so the result is deterministic.
 template <typename T>
-__device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch)
+__device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch, const T* Amat = nullptr)
 {
     const int n = tp.n, np = tp.n_pad, N3 = 3 * np;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const T* __restrict__ A = tp.ainv;
+    const T* __restrict__ A = Amat ? Amat : tp.ainv;
     if constexpr (sizeof(T) == 4) {
         const int ntile = (n + 127) >> 7;
         // ntile <= nw: warp w takes tile w % ntile and a share of the j range;
@@ -604,16 +618,28 @@ struct CellSolver {
                 }
                 if (eval_mode) {
                     uy = a->y[so + c * n + i] - xv;
+                } else if (T_.minv) {
+                    // right-hand side h M v_n + h^2 F_ext of M~ (y - x_n), solved below
+                    const T vv = a->v[so + c * n + i], fv = a->f[so + c * n + i];
+                    ut[e] = h * __ldg(&T_.mass[i]) * vv + h * h * fv;
                 } else {
                     const T vv = a->v[so + c * n + i], fv = a->f[so + c * n + i];
                     uy = (h * vv + h * h * fv * __ldg(&T_.inv_mass[i])) * inv_ms;
                 }
+            } else if (T_.minv && !eval_mode) {
+                ut[e] = T(0);
             }
             XN[e] = xn;
             UYv[e] = uy;
             u[e] = eval_mode ? T(0) : uy;
         }
         __syncthreads();
+        if (T_.minv && !eval_mode) {
+            // beta_D > 0: y - x_n = M~^-1 (h M v_n + h^2 F_ext) (Eq. preOptimizationNewton)
+            contract_simt(T_, ut, UYv, TRIv, T_.minv);
+            for (int e = tid; e < N3; e += NT) u[e] = UYv[e];
+            __syncthreads();
+        }
         // learned warm start: u = u_y + R MLP(features at y)
         // temporal warm start: u = u_y + (x_n - y_{n-1}) of this cell's previous step
         const int ws = (!eval_mode && !hist && T_.mlp) ? T_.ws_mode : 0;
