@@ -190,11 +190,15 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
    not fit in shared memory, plus the work counters) is a fixed 32 MiB __device__
    array compiled into the library, held by every GPU that loads the library until
    the process exits.  Arguments, layout, results and errors are those of
-   npfem_step (same kernel; with large meshes it may run fewer persistent blocks so
-   that their slots fit), plus INVALID_ARG when one block's scratch exceeds the
-   array.  The first call on a device looks up the array's device address (a host
-   reference to it is not a device pointer); make that first call before any
-   stream capture.  All calls on a device share the array and it keeps the last
+   npfem_step, with these differences: every group runs the persistent SIMT solver
+   kernel (NPFEM_PREC_BF16 handles included, which then contract A^-1 in FP32 on the
+   SIMT pipes instead of the tensor-core cluster kernel), one launch per distinct
+   tuned block size as npfem_step launches its SIMT groups; the temporal warm start
+   (opts.warm_history) is not used; with large meshes it may run fewer persistent
+   blocks so that their slots fit; and it returns INVALID_ARG when one block's
+   scratch exceeds the array.  Every call looks up the array's device address on
+   the handles' device (a host reference to it is not a device pointer; the lookup
+   allocates nothing).  All calls on a device share the array and it keeps the last
    call's contents (the work counters are cleared on `stream` before each launch):
    calls whose kernels overlap on the GPU race and must be avoided. */
 int npfem_step_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
@@ -282,6 +286,63 @@ int npfem_ws_guess(npfem_handle* h, int n_cells, const float* x, const float* v,
    iteration limit): returns NPFEM_ERR_TIMEOUT and clears the flag if so, else 0.
    Errors: INVALID_ARG, CUDA. */
 int npfem_check_device(npfem_handle* h);
+
+/* ---- immersed-boundary force step (Sec. 2.3), upstream of npfem_step ------------
+   A uniform fluid lattice: node (i, j, k) sits at origin + dx (i, j, k), 0 <= i < nx,
+   0 <= j < ny, 0 <= k < nz (um).  Lattice fields are FP32 device arrays, node-major
+   with x fastest: index ((k ny + j) nx + i), then the components of the node:
+     stress:            8 floats per node, (xx, yy, zz, xy, xz, yz, unused, unused);
+     velocity or force: 4 floats per node, (x, y, z, unused).
+   Each membrane vertex X_k sees the 4 x 4 x 4 lattice nodes around it, weighted by
+   the product of the paper's one-dimensional four-point kernel w(r) (Sec. 2.3) at
+   the node's offset in lattice units; nodes outside the lattice contribute nothing
+   (a lattice should cover the cells with two nodes to spare).  A_k is a third of the
+   areas of the triangles around vertex k and n_k its unit area-weighted normal, both
+   at the positions x.  Vertex arrays (x, forces, velocities) use the state's SoA
+   layout and group concatenation; FP32-state handles only.  The calls are
+   asynchronous on `stream` and allocate nothing.  Errors: INVALID_ARG, CUDA. */
+typedef struct {
+    double origin[3]; /* position of node (0, 0, 0), um */
+    double dx;        /* lattice spacing, um (> 0) */
+    int32_t nx, ny, nz;
+    int32_t reserved; /* set to 0 */
+} npfem_lattice;
+
+/* External force of Eq. Fext from a lattice stress field (pN/um^2, or per unit
+   density with rho_fluid the fluid density):
+   F_k = rho_fluid A_k (sum over the stencil of sigma(x) w w w) n_k into f_ext (pN).
+   mode 0: the whole stencil (Eq. Fext); mode 1: only the stencil nodes on the outside
+   of the membrane ((x - X_k) . n_k > 0), their weights renormalised to sum to one
+   (the paper disregards the interior fluid); mode 2: the stress of the exterior
+   stencil node farthest from X_k (the paper's stabler variant; the first in z, y, x
+   order among equals). */
+int npfem_ibm_forces(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, const float* x,
+                     const npfem_lattice* lattice, const float* sigma, double rho_fluid, int mode, float* f_ext,
+                     void* stream);
+
+/* Interpolation of a lattice velocity to the vertices (Sec. 2.3):
+   u(X_k) = sum over the stencil of u(x) w w w, into u_vertex (SoA). */
+int npfem_ibm_interpolate(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, const float* x,
+                          const npfem_lattice* lattice, const float* u_lattice, float* u_vertex, void* stream);
+
+/* Multi-direct forcing (Sec. 2.3, Steps 0-5): with the fluid velocity u* on the
+   lattice (u_lattice) and the membrane velocity U_k at the vertices (u_vertex, e.g.
+   the v of npfem_step), f_0 = (U_k - u*(X_k))/dt_fluid, then `cycles` times: spread
+   f_l(x) = sum_k f_l(X_k) (w w w / dx^3) A_k dx (a membrane one spacing thick),
+   u_l = u* + dt_fluid f_l, f_{l+1}(X_k) = f_l(X_k) + (U_k - u_l(X_k))/dt_fluid.
+   Writes the final Lagrangian force f_L to f_vertex (SoA, um/us^2) and its spread, the
+   body force f_imm of the fluid step, to f_lattice (4 floats per node; also used as
+   the working lattice, so it must not alias u_lattice).  Spreading adds with atomics,
+   so f_lattice is reproducible to FP32 rounding only.  cycles in 0..1000. */
+int npfem_ibm_forcing(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, const float* x,
+                      const float* u_vertex, const npfem_lattice* lattice, const float* u_lattice, double dt_fluid,
+                      int cycles, float* f_vertex, float* f_lattice, void* stream);
+
+/* Test hook for the reporting path of the bounded device waits: sets the handle's
+   device-wait flag exactly as a kernel whose wait gave up sets it (a host-side write;
+   no device work is made to wait), so that the next npfem_check_device returns
+   NPFEM_ERR_TIMEOUT.  Synchronises the handle's device.  Errors: INVALID_ARG, CUDA. */
+int npfem_flag_wait_timeout(npfem_handle* h);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* npfem_last_error(void);

@@ -38,6 +38,16 @@ class Opts(C.Structure):
                 ("fill_idle_sms", C.c_int32), ("warm_history", C.c_int32)]
 
 
+class Lattice(C.Structure):
+    """npfem_lattice: node (i, j, k) at origin + dx (i, j, k)."""
+    _fields_ = [("origin", C.c_double * 3), ("dx", C.c_double), ("nx", C.c_int32), ("ny", C.c_int32),
+                ("nz", C.c_int32), ("reserved", C.c_int32)]
+
+
+def lattice(origin, dx, shape_xyz) -> Lattice:
+    return Lattice((C.c_double * 3)(*[float(o) for o in origin]), float(dx), *[int(s) for s in shape_xyz], 0)
+
+
 class CellStats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("evaluations", C.c_int32), ("status", C.c_int32),
                 ("residual", C.c_float), ("objective", C.c_double), ("volume", C.c_double)]
@@ -52,7 +62,8 @@ EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", 
            "npfem_check_device", "npfem_mlp_nparam", "npfem_ws_features", "npfem_mlp_loss_grad", "npfem_mlp_adam",
            "npfem_mlp_predict", "npfem_set_warmstart", "npfem_ws_guess", "npfem_launch_count",
            "npfem_kernel_timing", "npfem_kernel_times", "npfem_graph_create", "npfem_graph_launch",
-           "npfem_graph_destroy", "npfem_kernel_time_last", "npfem_autotune", "npfem_get_tuning")
+           "npfem_graph_destroy", "npfem_kernel_time_last", "npfem_autotune", "npfem_get_tuning",
+           "npfem_flag_wait_timeout", "npfem_ibm_forces", "npfem_ibm_interpolate", "npfem_ibm_forcing")
 
 
 def lib_path() -> str:
@@ -87,6 +98,10 @@ def lib():
         L.npfem_get_inverse.argtypes = [vp, vp]
         L.npfem_get_rest_info.argtypes = [vp, vp, vp]
         L.npfem_check_device.argtypes = [vp]
+        L.npfem_flag_wait_timeout.argtypes = [vp]
+        L.npfem_ibm_forces.argtypes = [vp, i32, vp, vp, C.POINTER(Lattice), vp, C.c_double, i32, vp, vp]
+        L.npfem_ibm_interpolate.argtypes = [vp, i32, vp, vp, C.POINTER(Lattice), vp, vp, vp]
+        L.npfem_ibm_forcing.argtypes = [vp, i32, vp, vp, vp, C.POINTER(Lattice), vp, C.c_double, i32, vp, vp, vp]
         L.npfem_mlp_nparam.argtypes = []
         L.npfem_ws_features.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
         L.npfem_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
@@ -191,6 +206,10 @@ class Handle:
         """Raises NpfemError(-5) if a bounded device wait of a previous step gave up."""
         _check(lib().npfem_check_device(self._h))
 
+    def flag_wait_timeout(self):
+        """Sets the device-wait flag as a timed-out wait would (tests the reporting path)."""
+        _check(lib().npfem_flag_wait_timeout(self._h))
+
     def inverse(self) -> np.ndarray:
         out = np.zeros((self.n, self.n))
         _check(lib().npfem_get_inverse(self._h, out.ctypes.data))
@@ -289,6 +308,34 @@ class StepGraph:
             self.close()
         except Exception:
             pass
+
+
+def _groups(handles, cells_per_group):
+    handles = list(handles)
+    arr = (C.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    cells = (C.c_int32 * len(handles))(*[int(c) for c in cells_per_group])
+    return arr, len(handles), cells
+
+
+def ibm_forces(handles, cells_per_group, x, lat: Lattice, sigma, f_out, rho_fluid=1.0, mode=0, stream=None):
+    """npfem_ibm_forces: Eq. Fext from a lattice stress field into f_out (device SoA)."""
+    arr, ng, cells = _groups(handles, cells_per_group)
+    _check(lib().npfem_ibm_forces(arr, ng, cells, _addr(x), C.byref(lat), _addr(sigma), float(rho_fluid), int(mode),
+                                  _addr(f_out), _addr(stream)))
+
+
+def ibm_interpolate(handles, cells_per_group, x, lat: Lattice, u_lattice, u_out, stream=None):
+    arr, ng, cells = _groups(handles, cells_per_group)
+    _check(lib().npfem_ibm_interpolate(arr, ng, cells, _addr(x), C.byref(lat), _addr(u_lattice), _addr(u_out),
+                                       _addr(stream)))
+
+
+def ibm_forcing(handles, cells_per_group, x, u_vertex, lat: Lattice, u_lattice, dt_fluid, cycles, f_vertex, f_lattice,
+                stream=None):
+    """npfem_ibm_forcing: multi-direct forcing; writes f_vertex (SoA) and f_lattice."""
+    arr, ng, cells = _groups(handles, cells_per_group)
+    _check(lib().npfem_ibm_forcing(arr, ng, cells, _addr(x), _addr(u_vertex), C.byref(lat), _addr(u_lattice),
+                                   float(dt_fluid), int(cycles), _addr(f_vertex), _addr(f_lattice), _addr(stream)))
 
 
 def step_static(handles, cells_per_group, x, v, f, dt: float, stream=None, stats=None):
