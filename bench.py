@@ -18,11 +18,24 @@ Legs:
             inside the timed region
   plain     the plain FP32 GPU path (FP32 SIMT contraction, first guess y), same
             cells, steps and residual tolerance
+  legs      the same comparison (chosen vs plain, equal final residual) on the other
+            workloads of the scope: the force noise redrawn every step ("regen"), the
+            chosen form with one refinement sweep of the tensor-core contraction
+            ("refine1"), 16384 cells under N(0, 2 pN) + 1000/s shear ("c4"), and 4096
+            cells of mixed resolution, 40 % 258, 40 % 642, 20 % 2562 vertices ("c3")
   cpu_baseline / --impl reference
             the FP64 CPU oracle on this machine's cores, on a bounded sample
 
+Roofline: algorithmic bytes per step follow the scope's count, per cell of n
+vertices 5*12n (x_n, v_n, F_ext in; x, v out) + k (4m + 6)*12n (the L-BFGS history
+streamed twice, x, grad, d read, s, y, x written per iteration) + l*24n (x_t read and
+the gradient written per evaluation), with k and l the iterations and evaluations
+per cell averaged over every timed step; the library's trajectory state (the last
+correction and the positions' rounding residues, 6*12n per cell) is reported apart
+as impl_bytes.
+
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--cells C]
-                [--precision bf16|fp32|fp64] [--warmstart learned|none]
+                [--precision bf16|fp32|fp64] [--warmstart learned|none] [--legs all|none|a,b]
 """
 from __future__ import annotations
 
@@ -41,10 +54,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RBC-steps/s (642-vtx cells, equal accuracy), chosen vs plain form, % roofline"
-# DRAM bytes (read + write) per launch of the cluster kernel at 1024 cells, from
+# DRAM bytes (read + write) of the solver launches of one step, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of this code, keyed by
-# (warm start, temporal warm start).  Set to None when the kernel changes.
-NCU_TRAFFIC_TC = {}
+# (cells, precision, temporal warm start, noise redrawn).  Emptied when a kernel changes.
+NCU_TRAFFIC = {}
 DT = 0.1
 N_VERTS = 642
 
@@ -66,6 +79,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--legs", default="all", help="extra workload legs: all, none, or a comma list of regen, "
+                    "refine1, c4, c3")
     ap.add_argument("--force-noise-regen", type=int, default=0,
                     help="1: the N(0, 0.5 pN) force noise is redrawn every step (4 draws used in turn, copied in "
                          "outside the step's events); 0: the force is fixed over the run")
@@ -171,14 +186,20 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(n, m, stats_iters, stats_evals, cells, history=False):
-    """Per-launch algorithmic bytes of the step (FP32): per cell 5*12n for x_n, v_n,
+def algorithmic_bytes(n, m, iters, evals, cells):
+    """Algorithmic bytes of one step (FP32) for `cells` cells of n vertices that took
+    `iters` iterations and `evals` evaluations in total: per cell 5*12n for x_n, v_n,
     F_ext in and x, v out; per iteration (4m + 6)*12n (the L-BFGS history streamed
-    twice, plus x, grad, d reads and s, y, x writes); per evaluation 2*12n.  With the
-    temporal warm start, per cell 6*12n more: the last correction and the positions'
-    rounding residues with their FP32 values, each read and written."""
+    twice, plus x, grad, d reads and s, y, x writes); per evaluation 2*12n."""
     vb = 12 * n
-    return cells * (11 if history else 5) * vb + stats_iters * (4 * m + 6) * vb + stats_evals * 2 * vb
+    return cells * 5 * vb + iters * (4 * m + 6) * vb + evals * 2 * vb
+
+
+def trajectory_bytes(n, cells):
+    """Bytes of the library's trajectory state per step (not algorithmic): the last
+    correction and the positions' rounding residues with their FP32 values, each read
+    and written, 6*12n per cell."""
+    return cells * 6 * 12 * n
 
 
 def peaks():
@@ -236,53 +257,84 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------
 # GPU legs
 # ----------------------------------------------------------------------------------
-def device_leg(N, W, handle, pop, cells, steps, warmup, torch, flush, kernel_times=False, graph=False, fpool=None):
-    xs = torch.tensor(W.to_soa(pop["x"][:cells]), dtype=torch.float32, device="cuda")
-    vs = torch.tensor(W.to_soa(pop["v"][:cells]), dtype=torch.float32, device="cuda")
-    fs = torch.tensor(W.to_soa(pop["f"][:cells]), dtype=torch.float32, device="cuda")
-    st = torch.zeros((cells, 32), dtype=torch.uint8, device="cuda")
+def soa_concat(W, pops, key, counts=None):
+    """Groups' [cells, n, 3] arrays in the library's concatenated SoA layout."""
+    counts = counts or [p["x"].shape[0] for p in pops]
+    return np.concatenate([W.to_soa(p[key][:c]).ravel() for p, c in zip(pops, counts)])
+
+
+def device_leg(N, W, handles, pops, counts, steps, warmup, torch, flush, kernel_times=False, graph=False,
+               fpools=None, force_fn=None):
+    """Warm-up steps, then `steps` timed steps of every group (CUDA events on the launch
+    stream, L2 flushed before each).  fpools: per group, force draws used in turn (the
+    noise redrawn every step; copied in outside the timed events), or None.
+    force_fn(k, xs, fs, fdraw): computes step k's force into fs from the current
+    positions (timed with its own events, outside the step's).  Returns the step
+    times, the solver-launch times and per-step statistics."""
+    dev = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    xs, vs, fs = dev(soa_concat(W, pops, "x", counts)), dev(soa_concat(W, pops, "v", counts)), dev(soa_concat(W, pops, "f", counts))
+    total = sum(counts)
+    st = torch.zeros((total, 32), dtype=torch.uint8, device="cuda")
+    st_all = torch.zeros((steps, total, 32), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    # forces redrawn every step: device copies of the draws, copied into fs before a step
-    fdev = [torch.tensor(W.to_soa(a), dtype=torch.float32, device="cuda") for a in fpool] if fpool else None
-    for k in range(warmup):
-        if fdev:
+    fdev = None
+    if fpools:
+        ndraw = len(fpools[0])
+        fdev = [dev(np.concatenate([W.to_soa(fp[k][:c]).ravel() for fp, c in zip(fpools, counts)]))
+                for k in range(ndraw)]
+    def set_force(k):
+        if force_fn is not None:
+            force_fn(k, xs, fs, fdev[k % len(fdev)] if fdev else None)
+        elif fdev:
             fs.copy_(fdev[k % len(fdev)])
-        N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
+
+    for k in range(warmup):
+        set_force(k)
+        N.step(handles, counts, xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
     torch.cuda.synchronize()
+    h0 = handles[0]
     if kernel_times:
         # with a graph the event pair is captured and re-recorded by every replay
-        handle.kernel_timing(1 if graph else steps)
-    g = N.StepGraph([handle], [cells], xs, vs, fs, DT, steps=1, stats=st) if graph else None
+        h0.kernel_timing(1 if graph else steps)
+    g = N.StepGraph(handles, counts, xs, vs, fs, DT, steps=1, stats=st) if graph else None
     kms = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = N.launch_count()
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for k in range(steps):
-        if fdev:
-            fs.copy_(fdev[(warmup + k) % len(fdev)])
+        fev[k][0].record(stream)
+        set_force(warmup + k)
+        fev[k][1].record(stream)
         flush.zero_()  # writes a buffer larger than L2 between timed steps
         ev[k][0].record(stream)
         if g is not None:
             g.launch(stream.cuda_stream)
         else:
-            N.step([handle], [cells], xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
+            N.step(handles, counts, xs, vs, fs, DT, stream=stream.cuda_stream, stats=st)
         ev[k][1].record(stream)
+        st_all[k].copy_(st)  # outside the events
         if g is not None and kernel_times:
-            kms.append(handle.kernel_time_last())  # waits for this step
+            kms.append(h0.kernel_time_last())  # waits for this step
     torch.cuda.synchronize()
     launches = N.launch_count() - launches0
     if g is not None:
         g.close()
     times = [a.elapsed_time(b) for a, b in ev]
+    force_ms = float(np.mean([a.elapsed_time(b) for a, b in fev])) if force_fn is not None else None
     ktimes = None
     if kernel_times:
-        ktimes = np.array(kms) if g is not None else handle.kernel_times(steps)
-        handle.kernel_timing(0)
-    # statistics of the last step (per-launch work for the roofline)
-    s = st.cpu().numpy().view(N.CELL_STATS_DTYPE).reshape(cells)
-    statuses = np.array([int((s["status"] == q).sum()) for q in range(4)], dtype=np.int64)
-    return {"times": times, "iters": int(s["iterations"].sum()), "evals": int(s["evaluations"].sum()),
-            "statuses": statuses, "res_max": float(s["residual"].max()), "launches": launches,
-            "kernel_ms": ktimes}
+        ktimes = np.array(kms) if g is not None else h0.kernel_times(steps)
+        h0.kernel_timing(0)
+    s = st_all.cpu().numpy().view(N.CELL_STATS_DTYPE).reshape(steps, total)
+    # per group: iterations and evaluations summed over cells, averaged over the timed steps
+    grp, off = [], 0
+    for c in counts:
+        grp.append((float(s["iterations"][:, off:off + c].sum(1).mean()), float(s["evaluations"][:, off:off + c].sum(1).mean())))
+        off += c
+    statuses = np.array([int((s["status"][-1] == q).sum()) for q in range(4)], dtype=np.int64)
+    return {"times": times, "groups": grp, "iters": sum(a for a, _ in grp), "evals": sum(b for _, b in grp),
+            "statuses": statuses, "res_max": float(s["residual"].max()), "launches": launches, "kernel_ms": ktimes,
+            "ms_per_step": float(np.mean(times)), "force_ms": force_ms}
 
 
 def e2e_leg(N, W, handle, pop, cells, steps, warmup, torch, fpool=None):
@@ -310,14 +362,123 @@ def e2e_leg(N, W, handle, pop, cells, steps, warmup, torch, fpool=None):
 
 def train_warm_start(handle, rank, train_steps, vertices):
     """Trains the warm-start network on trajectories of the plain solver (1000 other
-    cells, 200 steps, seed 100 + rank) and installs it; returns a summary."""
+    cells, 200 steps, seed 100 + rank); returns the parameters and a summary."""
     from paper_1903_06479_gb300 import learn
     t0 = time.perf_counter()
     P, info = learn.train_warmstart(handle, n_cells=1000, steps=200, seed=100 + rank, train_steps=train_steps,
                                     vertices_per_step=vertices)
-    handle.set_warmstart(P, 1)
-    return {"train_s": time.perf_counter() - t0, "samples": info["samples"], "step_pairs": info["step_pairs"],
-            "loss_init": info["loss_init"], "loss_final": info["loss_final"], "network": "9-64-64-3 tanh, BF16 operands"}
+    return P, {"train_s": time.perf_counter() - t0, "samples": info["samples"], "step_pairs": info["step_pairs"],
+               "loss_init": info["loss_init"], "loss_final": info["loss_final"],
+               "network": "9-64-64-3 tanh, BF16 operands"}
+
+
+IBM_DX = 1.0  # um, lattice spacing of the benchmark's stress field
+IBM_FORCES = ("Eq. Fext on the GPU (npfem_ibm_forces, four-point stencil) from a plasma shear-stress lattice "
+              "(dx 1 um; sigma_xy = eta gamma(z), gamma rising linearly from 10 to 1000 1/s across the 100 um box) "
+              "at the current positions every step, plus N(0,0.5 pN) noise redrawn every step (4 draws used in turn)")
+
+
+def ibm_force_fn(N, W, torch, handles, counts):
+    """Step-k force of the regenerated-force recipe: Eq. Fext from an analytic
+    shear-stress lattice at the current positions (explicit coupling), plus the k-th
+    noise draw.  Returns (force_fn, lattice description)."""
+    lo, hi = -10.0, 110.0
+    nn = int(round((hi - lo) / IBM_DX)) + 1
+    z = lo + IBM_DX * np.arange(nn)
+    gamma = (10.0 + 990.0 * (z - 0.0) / 100.0) * 1e-6  # 1/s -> 1/us, linear in z
+    s8 = torch.zeros((nn, nn, nn, 8), dtype=torch.float32, device="cuda")
+    s8[..., 3] = torch.tensor(W.PLASMA_ETA * gamma, dtype=torch.float32, device="cuda")[:, None, None]
+    lat = N.lattice((lo, lo, lo), IBM_DX, (nn, nn, nn))
+    stream = torch.cuda.current_stream()
+
+    def fn(k, xs, fs, fdraw):
+        N.ibm_forces(handles, counts, xs, lat, s8, fs, stream=stream.cuda_stream)
+        if fdraw is not None:
+            fs.add_(fdraw)
+
+    return fn, {"nodes": nn ** 3, "dx_um": IBM_DX, "bytes": nn ** 3 * 32}
+
+
+def make_chosen(N, W, pops, counts, precision, history, refine, ws_params, local, torch, autotune=True, **mat):
+    """Handles of the chosen form (one per group), warm-start network installed on the
+    642-vertex groups, launch shapes picked by the autotuner from a state 5 steps past
+    the start; returns (handles, shapes)."""
+    hs = []
+    for p in pops:
+        o = N.default_opts(precision=precision, tol=1e-6, max_iter=50, refine=refine, warm_history=history)
+        h = N.Handle(p["rest"], p["tris"], N.material(**mat), o, dt=DT, device=local)
+        if ws_params is not None and h.n == N_VERTS and precision != "fp64":
+            h.set_warmstart(ws_params, 1)
+        hs.append(h)
+    shapes = None
+    if autotune:
+        dev = lambda k: torch.tensor(soa_concat(W, pops, k, counts), dtype=torch.float32, device="cuda")
+        tx, tv, tf = dev("x"), dev("v"), dev("f")
+        for _ in range(5):
+            N.step(hs, counts, tx, tv, tf, DT)
+        shapes = N.autotune(hs, counts, tx, tv, tf, DT, trial_steps=4)
+        del tx, tv, tf
+    return hs, shapes
+
+
+def make_plain(N, pops, local, **mat):
+    return [N.Handle(p["rest"], p["tris"], N.material(**mat),
+                     N.default_opts(precision="fp32", tol=1e-6, max_iter=50, warm_history=0), dt=DT, device=local)
+            for p in pops]
+
+
+def roofline(pk, pk_kind, groups_n, leg, m, history, cells_by_group, kernel_name, traffic=None):
+    """HBM roofline of the solver launches of one step: the scope's algorithmic bytes
+    (mean over the timed steps) over the mean duration of the solver launches."""
+    alg = sum(algorithmic_bytes(n, m, it, ev, c) for n, (it, ev), c in zip(groups_n, leg["groups"], cells_by_group))
+    kms = leg["kernel_ms"]
+    t = float(np.mean(kms)) / 1e3 if kms is not None and len(kms) else leg["ms_per_step"] / 1e3
+    achieved = alg / t / 1e9
+    impl = sum(trajectory_bytes(n, c) for n, c in zip(groups_n, cells_by_group)) if history else 0
+    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+            "peak_source": (f"{pk_kind} (HBM copy bandwidth, MEASURED_PEAKS.json)" if pk_kind == "measured"
+                            else "fallback (6.8 TB/s)"),
+            "kernel": kernel_name, "kernel_ms_mean": t * 1e3, "algorithmic_bytes_per_launch": alg,
+            "impl_bytes_per_launch": impl}
+
+
+def compare_leg(N, W, torch, name, pops, counts, args, flush, ws_params, local, pk, pk_kind, fpools=None,
+                refine=0, plain=True, mat=None, ibm=False):
+    """Chosen form and plain FP32 path on the same cells, steps and residual tolerance."""
+    mat = mat or {}
+    hs, shapes = make_chosen(N, W, pops, counts, args.precision, args.history, refine, ws_params, local, torch, **mat)
+    ffn, lat_info = ibm_force_fn(N, W, torch, hs, counts) if ibm else (None, None)
+    ch = device_leg(N, W, hs, pops, counts, args.steps, args.warmup, torch, flush, kernel_times=True,
+                    graph=bool(args.graph), fpools=fpools, force_fn=ffn)
+    total = sum(counts)
+    ns = [p["rest"].shape[0] for p in pops]
+    out = {"cells": total, "groups": [{"n_verts": n, "cells": c} for n, c in zip(ns, counts)],
+           "chosen": {"value": total * args.steps / (sum(ch["times"]) / 1e3), "ms_per_step": ch["ms_per_step"],
+                      "iterations_per_cell": ch["iters"] / total, "evaluations_per_cell": ch["evals"] / total,
+                      "residual_max": ch["res_max"], "status_counts": ch["statuses"].tolist(),
+                      "launch_shapes": shapes},
+           "roofline": roofline(pk, pk_kind, ns, ch, 5, args.history, counts, "solver launches of one step "
+                                "(event pair around them)")}
+    if ibm:
+        verts = sum(n * c for n, c in zip(ns, counts))
+        out["ibm_forces"] = {"ms_mean": ch["force_ms"], "vertices": verts,
+                             "vertices_per_s": verts / (ch["force_ms"] / 1e3), "lattice": lat_info,
+                             "note": "npfem_ibm_forces plus the noise add, timed apart from the step"}
+    for h in hs:
+        h.close()
+    if plain:
+        hp = make_plain(N, pops, local, **mat)
+        pfn = ibm_force_fn(N, W, torch, hp, counts)[0] if ibm else None
+        pl = device_leg(N, W, hp, pops, counts, args.steps, args.warmup, torch, flush, fpools=fpools, force_fn=pfn)
+        out["plain"] = {"value": total * args.steps / (sum(pl["times"]) / 1e3), "ms_per_step": pl["ms_per_step"],
+                        "iterations_per_cell": pl["iters"] / total, "evaluations_per_cell": pl["evals"] / total,
+                        "residual_max": pl["res_max"], "status_counts": pl["statuses"].tolist()}
+        out["chosen_over_plain"] = out["chosen"]["value"] / out["plain"]["value"]
+        for h in hp:
+            h.close()
+    torch.cuda.synchronize()
+    return out
 
 
 def main():
@@ -333,31 +494,26 @@ def main():
     N.lib()
     cells = args.cells
     pop = W.population(N_VERTS, cells, seed=1 + rank, forces="shear", noise_pN=0.5)
-    opts = N.default_opts(precision=args.precision, tol=1e-6, max_iter=50, refine=0, warm_history=args.history)
-    handle = N.Handle(pop["rest"], pop["tris"], N.material(), opts, dt=DT, device=local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     fpool = W.noise_redrawn_forces(pop, cells, 7 + rank) if args.force_noise_regen else None
+    pk, pk_kind = peaks()
 
-    ws = None
+    ws, P = None, None
     if args.warmstart == "learned" and args.precision != "fp64":
-        ws = train_warm_start(handle, rank, args.ws_train_steps, args.ws_vertices)
-    shape = None
-    if args.autotune:
-        mk = lambda a: torch.tensor(W.to_soa(a), dtype=torch.float64 if args.precision == "fp64" else torch.float32,
-                                    device="cuda")
-        # trial steps from a state past the first few steps from rest (typical iteration counts)
-        tx, tv, tf = mk(pop["x"]), mk(pop["v"]), mk(pop["f"])
-        for _ in range(5):
-            N.step([handle], [cells], tx, tv, tf, DT)
-        shape = N.autotune([handle], [cells], tx, tv, tf, DT, trial_steps=4)[0]
-        del tx, tv, tf
+        o = N.default_opts(precision="fp32", tol=1e-6, max_iter=50)
+        htrain = N.Handle(pop["rest"], pop["tris"], N.material(), o, dt=DT, device=local)
+        P, ws = train_warm_start(htrain, rank, args.ws_train_steps, args.ws_vertices)
+        htrain.close()
+    hs, shapes = make_chosen(N, W, [pop], [cells], args.precision, args.history, 0, P, local, torch,
+                             autotune=bool(args.autotune))
+    handle = hs[0]
 
     barrier(pg)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        dl = device_leg(N, W, handle, pop, cells, args.steps, args.warmup, torch, flush, kernel_times=True,
-                        graph=bool(args.graph), fpool=fpool)
+        dl = device_leg(N, W, hs, [pop], [cells], args.steps, args.warmup, torch, flush, kernel_times=True,
+                        graph=bool(args.graph), fpools=[fpool] if fpool else None)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     barrier(pg)
@@ -369,42 +525,70 @@ def main():
     clocks = clk.summary()
 
     plain = None
-    if not args.no_plain and (args.precision != "fp32" or ws is not None):
-        hp = N.Handle(pop["rest"], pop["tris"], N.material(),
-                      N.default_opts(precision="fp32", tol=1e-6, max_iter=50, warm_history=0), dt=DT, device=local)
-        pl = device_leg(N, W, hp, pop, cells, args.steps, args.warmup, torch, flush, fpool=fpool)
+    if not args.no_plain and (args.precision != "fp32" or P is not None):
+        hp = make_plain(N, [pop], local)
+        pl = device_leg(N, W, hp, [pop], [cells], args.steps, args.warmup, torch, flush,
+                        fpools=[fpool] if fpool else None)
         plain = {"value": total_cells * args.steps / max_over_ranks(pg, sum(pl["times"]) / 1e3),
                  "unit": "RBC-steps/s", "form": "FP32 SIMT contraction, first guess y", "steps": args.steps,
                  "iterations_per_cell": pl["iters"] / cells, "evaluations_per_cell": pl["evals"] / cells,
                  "residual_max": pl["res_max"], "status_counts": pl["statuses"].tolist()}
-        del hp
+        hp[0].close()
 
     e2e = None
     if not args.no_e2e:
         barrier(pg)
-        # the device leg's steps of the same trajectory from the same start
+        # the device leg's steps of the same trajectory from the same start, on a fresh
+        # handle of the same form (its own trajectory state)
+        he, _ = make_chosen(N, W, [pop], [cells], args.precision, args.history, 0, P, local, torch, autotune=False)
+        if shapes is not None and not shapes[0]["tensor_core"]:
+            he = hs
         ke = args.steps
-        e_s, bi, bo = e2e_leg(N, W, handle, pop, cells, ke, args.warmup, torch, fpool=fpool)
+        e_s, bi, bo = e2e_leg(N, W, he[0], pop, cells, ke, args.warmup, torch, fpool=fpool)
         e_s = max_over_ranks(pg, e_s)
         e2e = {"value": total_cells * ke / e_s, "unit": "RBC-steps/s", "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "steps": ke}
 
-    pk, pk_kind = peaks()
-    m = opts.lbfgs_m
-    alg = algorithmic_bytes(N_VERTS, m, dl["iters"], dl["evals"], cells, history=bool(args.history))
-    kms = dl["kernel_ms"]
-    t_kernel = float(np.mean(kms)) / 1e3 if kms is not None and len(kms) else dev_s / args.steps
-    achieved = alg / t_kernel / 1e9
     kname = "cell_kernel_tc<float>" if args.precision == "bf16" else "cell_kernel"
     if args.precision == "bf16" and args.history:
-        kname = "first-iterate pass cell_kernel<float, 512> + cell_kernel_tc<float> (one event pair)"
-    traffic = None
-    if args.precision == "bf16" and cells == 1024 and NCU_TRAFFIC_TC is not None:
-        traffic = NCU_TRAFFIC_TC.get(("learned" if ws is not None else "none", args.history))
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-            "peak_source": f"{pk_kind} (HBM copy bandwidth, MEASURED_PEAKS.json)" if pk_kind == "measured" else pk_kind,
-            "kernel": kname, "kernel_ms_mean": t_kernel * 1e3, "algorithmic_bytes_per_launch": alg}
+        kname = "solver launches of one step: first-iterate pass cell_kernel<float, 512>, cell_kernel_tc<float, 32>, " \
+                "idle-SM cell_kernel (one event pair)"
+    traffic = NCU_TRAFFIC.get((cells, args.precision, args.history, args.force_noise_regen)) if NCU_TRAFFIC else None
+    roof = roofline(pk, pk_kind, [N_VERTS], dl, 5, args.history, [cells], kname, traffic)
+
+    # the other workloads of the scope, each chosen vs plain at equal residual
+    legs = {}
+    want = set() if args.legs == "none" else (
+        {"regen", "refine1", "c4", "c3"} if args.legs == "all" else set(args.legs.split(",")))
+    if world > 1:
+        want = set()  # the extra legs are single-GPU comparisons
+    if "regen" in want and not args.force_noise_regen:
+        # forces regenerated every step from the current positions (explicit coupling):
+        # the immersed-boundary traction of Eq. Fext plus redrawn noise
+        noise = [d - pop["f_shear"][:cells] for d in W.noise_redrawn_forces(pop, cells, 7 + rank)]
+        legs["regen"] = compare_leg(N, W, torch, "regen", [pop], [cells], args, flush, P, local, pk, pk_kind,
+                                    fpools=[noise], ibm=True)
+        legs["regen"]["forces"] = IBM_FORCES
+    if "refine1" in want and args.precision == "bf16":
+        legs["refine1"] = compare_leg(N, W, torch, "refine1", [pop], [cells], args, flush, P, local, pk, pk_kind,
+                                      refine=1, plain=False)
+        legs["refine1"]["form"] = "chosen form with one refinement sweep of the tensor-core contraction"
+    if "c4" in want:
+        p4 = W.population(N_VERTS, 16384, seed=3 + rank, forces="shear", gamma_fixed=1000.0, noise_pN=2.0)
+        legs["c4"] = compare_leg(N, W, torch, "c4", [p4], [16384], args, flush, P, local, pk, pk_kind)
+        legs["c4"]["workload"] = "16384 RBCs x 642-vertex discocyte, N(0,2 pN) + shear 1000/s (fixed), dt 0.1 us, tol 1e-6"
+        del p4
+    if "c3" in want:
+        n_all = 4096
+        c258, c642 = round(0.4 * n_all), round(0.4 * n_all)
+        c2562 = n_all - c258 - c642
+        # groups ordered largest mesh first: their cells take longest
+        p3 = [W.population(nv, c, seed=10 * (k + 1) + rank, forces="shear", noise_pN=0.5)
+              for k, (nv, c) in enumerate([(2562, c2562), (642, c642), (258, c258)])]
+        legs["c3"] = compare_leg(N, W, torch, "c3", p3, [c2562, c642, c258], args, flush, P, local, pk, pk_kind)
+        legs["c3"]["workload"] = (f"{n_all} RBCs of mixed resolution: {c2562} x 2562, {c642} x 642, {c258} x 258 "
+                                  "vertices, shear U(10,1000)/s + N(0,0.5 pN) (fixed), dt 0.1 us, tol 1e-6")
+        del p3
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -427,20 +611,21 @@ def main():
                 "config": {"workload": workload_name(cells, args.force_noise_regen),
                            "cells_per_gpu": cells, "precision": prec_name,
                            "forces": FORCES_REGEN if args.force_noise_regen else FORCES_FIXED,
-                           "warm_start": ("learned MLP" if ws is not None else "first guess y")
+                           "warm_start": ("learned MLP" if P is not None else "first guess y")
                            + (" (first step), then previous step's correction" if args.history else ""),
-                           "lbfgs_m": m,
+                           "lbfgs_m": 5, "refine": 0,
                            "launch": "CUDA graph of one step per timed step" if args.graph else "npfem_step per step",
-                           "launch_shape": shape if shape is not None else "default",
+                           "launch_shape": shapes[0] if shapes is not None else "default",
                            "l2": "flushed between timed steps (256 MB write)"},
                 "gpu_launches": dl["launches"],
                 "wall_s": t_wall,
                 "per_step_ms": {"median": float(np.median(times)), "min": float(np.min(times)),
                                 "max": float(np.max(times))},
                 "solver": {"iterations_per_cell": dl["iters"] / cells, "evaluations_per_cell": dl["evals"] / cells,
+                           "averaged_over": f"{args.steps} timed steps",
                            "status_counts": dl["statuses"].tolist(), "residual_max": dl["res_max"]},
                 "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "plain": plain,
-                "warm_start": ws}
+                "warm_start": ws, "legs": legs}
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
