@@ -413,7 +413,44 @@ double or_energy_vol(const or_model *m, const double *x, double *grad, double *v
 /* g = (1/2h^2) tr((x-y)^T M~ (x-y)) + PD energies + non-PD energies.           */
 /* parts (optional, 6): inertia, area, skalak, bend, volume-energy, V.          */
 /* ------------------------------------------------------------------------ */
+/* Collision energy of Sec. 3.3 (non-PD part of Eq. GeneralizedObjectiveFunction):  */
+/* vertex i with a plane (unit normal n_i, offset c_i; n_i = 0: none) penetrates    */
+/* the neighbouring body while d_i = c_i - n_i . x_i > 0; its desired position p_i   */
+/* is x_i moved onto the plane, so E = (w/2) |p_i - x_i|^2 = (w/2) d_i^2 and the force */
+/* w (p_i - x_i) = w d_i n_i.  The test d_i > 0 is made at every evaluation, which   */
+/* cancels the term as soon as the vertex no longer penetrates.                       */
+double or_energy_collision(const or_model *m, const double *x, const double *col, double wcol, double *grad)
+{
+    double E = 0.0;
+    if (!col) return 0.0;
+    for (int i = 0; i < m->n; ++i) {
+        const double *pl = col + 4 * i;
+        if (pl[0] == 0.0 && pl[1] == 0.0 && pl[2] == 0.0) continue;
+        double d = pl[3] - v3dot(pl, x + 3 * i);
+        if (!(d > 0.0)) continue;
+        E += 0.5 * wcol * d * d;
+        if (grad)
+            for (int r = 0; r < 3; ++r) grad[3 * i + r] -= wcol * d * pl[r];
+    }
+    return E;
+}
+
+static double objective_col(const or_model *m, const double *x, const double *y, double *grad, double *parts, int *bad,
+                            const double *col, double wcol);
+
 double or_objective(const or_model *m, const double *x, const double *y, double *grad, double *parts, int *bad)
+{
+    return objective_col(m, x, y, grad, parts, bad, NULL, 0.0);
+}
+
+double or_objective_col(const or_model *m, const double *x, const double *y, double *grad, double *parts, int *bad,
+                        const double *col, double wcol)
+{
+    return objective_col(m, x, y, grad, parts, bad, col, wcol);
+}
+
+static double objective_col(const or_model *m, const double *x, const double *y, double *grad, double *parts, int *bad,
+                            const double *col, double wcol)
 {
     int n = m->n;
     double h2 = m->h * m->h;
@@ -431,8 +468,9 @@ double or_objective(const or_model *m, const double *x, const double *y, double 
     double Eb = or_energy_bend(m, x, grad);
     double V = 0.0;
     double Ev = or_energy_vol(m, x, grad, &V);
+    double Ec = or_energy_collision(m, x, col, wcol, grad);
     if (parts) { parts[0] = Ein; parts[1] = Ea; parts[2] = Es; parts[3] = Eb; parts[4] = Ev; parts[5] = V; }
-    return Ein + Ea + Es + Eb + Ev;
+    return Ein + Ea + Es + Eb + Ev + Ec;
 }
 
 /* internal energy only (no inertia), gradient overwritten */
@@ -695,7 +733,16 @@ static double dot3n(const double *a, const double *b, int n)
     return s;
 }
 
+static int solve_col(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st, const double *col,
+                     double wcol);
+
 int or_solve(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st)
+{
+    return solve_col(m, x, y, o, st, NULL, 0.0);
+}
+
+static int solve_col(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st, const double *col,
+                     double wcol)
 {
     int n = m->n, N = 3 * n, M = o->lbfgs_m;
     size_t vb = sizeof(double) * N;
@@ -705,7 +752,7 @@ int or_solve(const or_model *m, double *x, const double *y, const or_opts *o, or
     int head = 0, count = 0, bad = 0;
     st->iterations = 0; st->evaluations = 1; st->status = OR_OK;
     double parts[6];
-    double E = or_objective(m, x, y, g, parts, &bad);
+    double E = objective_col(m, x, y, g, parts, &bad, col, wcol);
     int k = 0;
     for (;;) {
         double r = or_residual(m, g);
@@ -741,7 +788,7 @@ int or_solve(const or_model *m, double *x, const double *y, const or_opts *o, or
         for (int hv = 0; hv <= o->max_halvings; ++hv) {
             for (int e = 0; e < N; ++e) xt[e] = x[e] + alpha * d[e];
             bad = 0;
-            Et = or_objective(m, xt, y, gt, parts, &bad);
+            Et = objective_col(m, xt, y, gt, parts, &bad, col, wcol);
             st->evaluations++;
             if (o->fixed_alpha || (!bad && Et <= E + o->c1 * alpha * gd)) { accepted = 1; break; }
             alpha *= 0.5;
@@ -827,7 +874,17 @@ void or_post_step(const or_model *m, const double *x, double *v, double kappa)
 
 /* One time step of Algorithm 1 for one cell: first guess, quasi-Newton solve,
    v_{n+1} = (x_{n+1} - x_n)/h, post-convergence dissipation. */
+int or_step_col(const or_model *m, double *x, double *v, const double *f, const or_opts *o, or_stats *st,
+                const double *col, double wcol);
+
 int or_step(const or_model *m, double *x, double *v, const double *f, const or_opts *o, or_stats *st)
+{
+    return or_step_col(m, x, v, f, o, st, NULL, 0.0);
+}
+
+/* The same step with collision planes (n x 4, or NULL) and weight wcol. */
+int or_step_col(const or_model *m, double *x, double *v, const double *f, const or_opts *o, or_stats *st,
+                const double *col, double wcol)
 {
     int n = m->n;
     size_t vb = sizeof(double) * 3 * n;
@@ -835,7 +892,7 @@ int or_step(const or_model *m, double *x, double *v, const double *f, const or_o
     memcpy(xn, x, vb);
     or_first_guess(m, xn, v, f, y);
     memcpy(x, y, vb);
-    int s = or_solve(m, x, y, o, st);
+    int s = solve_col(m, x, y, o, st, col, wcol);
     if (s == OR_NONFINITE) memcpy(x, xn, vb); /* keep x_n for a failed cell */
     for (int i = 0; i < 3 * n; ++i) v[i] = (x[i] - xn[i]) / m->h;
     or_post_step(m, x, v, m->mat[M_KAPPA]);
@@ -854,6 +911,8 @@ typedef struct {
     const or_opts *o;
     or_stats *st;
     int c0, c1, steps;
+    const double *col; /* ncells x n x 4 collision planes, or NULL */
+    double wcol;
 } or_job;
 
 static void *or_worker(void *arg)
@@ -862,19 +921,30 @@ static void *or_worker(void *arg)
     size_t N = 3 * (size_t)j->m->n;
     for (int c = j->c0; c < j->c1; ++c)
         for (int s = 0; s < j->steps; ++s)
-            or_step(j->m, j->x + c * N, j->v + c * N, j->f + c * N, j->o, j->st + c);
+            or_step_col(j->m, j->x + c * N, j->v + c * N, j->f + c * N, j->o, j->st + c,
+                        j->col ? j->col + (size_t)c * 4 * j->m->n : NULL, j->wcol);
     return NULL;
 }
 
+int or_step_batch_col(const or_model *m, int ncells, int steps, double *x, double *v, const double *f,
+                      const or_opts *o, or_stats *st, int nthreads, const double *col, double wcol);
+
 int or_step_batch(const or_model *m, int ncells, int steps, double *x, double *v, const double *f, const or_opts *o,
                   or_stats *st, int nthreads)
+{
+    return or_step_batch_col(m, ncells, steps, x, v, f, o, st, nthreads, NULL, 0.0);
+}
+
+int or_step_batch_col(const or_model *m, int ncells, int steps, double *x, double *v, const double *f,
+                      const or_opts *o, or_stats *st, int nthreads, const double *col, double wcol)
 {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > ncells) nthreads = ncells;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
     or_job *jobs = (or_job *)malloc(sizeof(or_job) * nthreads);
     for (int t = 0; t < nthreads; ++t) {
-        jobs[t] = (or_job){m, x, v, f, o, st, (int)((long)ncells * t / nthreads), (int)((long)ncells * (t + 1) / nthreads), steps};
+        jobs[t] = (or_job){m, x, v, f, o, st, (int)((long)ncells * t / nthreads), (int)((long)ncells * (t + 1) / nthreads),
+                           steps, col, wcol};
         pthread_create(&th[t], NULL, or_worker, &jobs[t]);
     }
     for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);

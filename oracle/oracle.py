@@ -96,6 +96,15 @@ def lib():
         L.or_best_rotation.argtypes = [P, dp, dp, dp, dp]
         L.or_ws_features.argtypes = [P, dp, dp, dp, dp]
         L.or_ws_guess.argtypes = [P, dp, dp, dp, dp, dp, C.c_int]
+        L.or_objective_col.restype = C.c_double
+        L.or_objective_col.argtypes = [P, dp, dp, P, P, P, P, C.c_double]
+        L.or_energy_collision.restype = C.c_double
+        L.or_energy_collision.argtypes = [P, dp, P, C.c_double, P]
+        L.or_step_col.restype = C.c_int
+        L.or_step_col.argtypes = [P, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats), P, C.c_double]
+        L.or_step_batch_col.restype = C.c_int
+        L.or_step_batch_col.argtypes = [P, C.c_int, C.c_int, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats), C.c_int,
+                                        P, C.c_double]
         L.or_step_batch.restype = C.c_int
         L.or_step_batch.argtypes = [P, C.c_int, C.c_int, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats), C.c_int]
         _lib = L
@@ -228,6 +237,22 @@ class Model:
         e = lib().or_objective(self._h, x, y, _ptr(g), _ptr(parts), C.byref(bad))
         return e, g, parts
 
+    def objective_col(self, x, y, col, wcol):
+        """g(x) and grad g(x) with the collision term of planes col [n, 4]."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        col = np.ascontiguousarray(col, dtype=np.float64)
+        g = np.zeros_like(x)
+        bad = C.c_int(0)
+        e = lib().or_objective_col(self._h, x, y, _ptr(g), None, C.byref(bad), _ptr(col), float(wcol))
+        return e, g
+
+    def energy_collision(self, x, col, wcol):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        col = np.ascontiguousarray(col, dtype=np.float64)
+        g = np.zeros_like(x)
+        return lib().or_energy_collision(self._h, x, _ptr(col), float(wcol), _ptr(g)), g
+
     def internal_energy(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64)
         g = np.zeros_like(x)
@@ -275,12 +300,18 @@ class Model:
         lib().or_ws_guess(self._h, np.ascontiguousarray(P, dtype=np.float64), *(np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, f)), x1, int(bf16_operands))
         return x1
 
-    def step_batch(self, x, v, f, opts: Opts | None = None, steps: int = 1, threads: int = 1):
-        """steps time steps of every cell of [cells, n, 3] arrays (the same force each step)."""
+    def step_batch(self, x, v, f, opts: Opts | None = None, steps: int = 1, threads: int = 1, col=None, wcol=0.0):
+        """steps time steps of every cell of [cells, n, 3] arrays (the same force each
+        step); col: optional collision planes [cells, n, 4] with weight wcol."""
         x = np.array(x, dtype=np.float64, order="C")
         v = np.array(v, dtype=np.float64, order="C")
         f = np.ascontiguousarray(f, dtype=np.float64)
         cells = x.shape[0]
         st = (Stats * cells)()
-        lib().or_step_batch(self._h, cells, steps, x, v, f, C.byref(opts or make_opts()), st, threads)
+        if col is None:
+            lib().or_step_batch(self._h, cells, steps, x, v, f, C.byref(opts or make_opts()), st, threads)
+        else:
+            col = np.ascontiguousarray(col, dtype=np.float64)
+            lib().or_step_batch_col(self._h, cells, steps, x, v, f, C.byref(opts or make_opts()), st, threads,
+                                    _ptr(col), float(wcol))
         return x, v, list(st)
