@@ -54,8 +54,11 @@ extern "C" {
 #define NPFEM_PREC_FP64 0 /* state, energies and the A^-1 contraction in FP64            */
 #define NPFEM_PREC_FP32 1 /* state and energies FP32 (sums FP64), A^-1 FP32 on the SIMT  */
                           /* pipes: the plain GPU path                                  */
-#define NPFEM_PREC_TF32 2 /* reserved: a TF32 row block of A^-1 does not fit in tensor    */
-                          /* memory; npfem_create rejects it                             */
+#define NPFEM_PREC_TF32 2 /* as FP32, but the A^-1 contraction runs on tcgen05 tensor    */
+                          /* cores in TF32 with FP32 accumulation: every persistent SIMT */
+                          /* block streams A^-1 (TF32, 128 x 32 tiles) from L2 through   */
+                          /* shared memory, `refine` refinement sweeps; up to 4096       */
+                          /* vertices (npfem_step_static contracts in FP32 instead)      */
 #define NPFEM_PREC_BF16 3 /* as FP32, but the A^-1 contraction runs on tcgen05 tensor    */
                           /* cores: BF16 A^-1 resident in tensor memory across a cluster */
                           /* of ceil(n/128) SMs, BF16 q, FP32 accumulation, `refine`     */
@@ -98,8 +101,8 @@ typedef struct {
    equal_mass: 1 = lump the mass equally, 0 = by barycentric rest area.
    armijo_noise: multiple of the estimated rounding error of g added to the
                  Armijo bound (FP32 energies); 0 = exact test.
-   refine: NPFEM_PREC_BF16 only: refinement sweeps of the tensor-core A^-1
-           contraction (0 or 1): r = A^-1 q, then r += A^-1 (q - H~ r).
+   refine: NPFEM_PREC_BF16 and NPFEM_PREC_TF32: refinement sweeps of the tensor-core
+           A^-1 contraction (0 or 1): r = A^-1 q, then r += A^-1 (q - H~ r).
    fill_idle_sms: NPFEM_PREC_BF16 only: 1 = SMs that the tensor-core clusters leave
            idle run the SIMT solver on the same cells (dynamic split), 0 = clusters only.
    warm_history: 1 = temporal warm start: when a call steps the same groups and cell
@@ -337,6 +340,33 @@ int npfem_ibm_interpolate(npfem_handle* const* meshes, int n_groups, const int32
 int npfem_ibm_forcing(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, const float* x,
                       const float* u_vertex, const npfem_lattice* lattice, const float* u_lattice, double dt_fluid,
                       int cycles, float* f_vertex, float* f_lattice, void* stream);
+
+/* ---- collisions between cells (Sec. 3.3) --------------------------------------
+   Detection: for every vertex of the call's cells (FP32 SoA positions x, groups as
+   in npfem_step), the nearest vertex of ANOTHER cell within `cutoff` (um; ties go to
+   the lowest vertex index, counting cells of all groups in order), found through a
+   uniform grid of bins of the cutoff's size.  planes (device, 4 floats per vertex,
+   vertices in the order of x): the unit outward normal n of the neighbouring cell at
+   that vertex (normalised area-weighted normal) and the plane's offset
+   n . (x_neighbour - x_0), x_0 the vertex's own cell's first vertex; (0, 0, 0, 0)
+   when there is no neighbour.  stats (device, 2 unsigned): vertices with a
+   neighbour, and vertices left out of the grid by a full bin (16 vertices per
+   hashed bin; nonzero means some neighbours may have been missed).  Grows a
+   library-owned table of 68 bytes per bin (bins: a power of two >= 2 vertices) on
+   meshes[0].  FP32-state handles.  Errors: INVALID_ARG, OOM, CUDA. */
+int npfem_collision_detect(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, const float* x,
+                           double cutoff, float* planes, unsigned int* stats, void* stream);
+
+/* Installs collision planes (device, the layout npfem_collision_detect writes, for
+   the same groups and cells) and their weight w_col (pN/um) for the npfem_step and
+   npfem_step_static calls whose first handle is h, until replaced or removed
+   (planes = NULL).  In those steps a vertex whose position x_i lies behind its plane
+   (d = offset - n . (x_i - x_0) > 0) adds the collision energy (w_col/2) d^2 and
+   force w_col d n to the objective (the non-PD term of Sec. 3.3), tested again at
+   every evaluation so that the term vanishes once the vertex no longer penetrates;
+   the constant H~ is unchanged.  The planes are read during the steps, so keep the
+   array alive; re-detect between steps.  Errors: INVALID_ARG. */
+int npfem_set_collisions(npfem_handle* h, const float* planes, double w_col);
 
 /* Test hook for the reporting path of the bounded device waits: sets the handle's
    device-wait flag exactly as a kernel whose wait gave up sets it (a host-side write;

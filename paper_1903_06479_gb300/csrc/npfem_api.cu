@@ -233,10 +233,6 @@ int check_opts(const npfem_opts* o)
         return fail(NPFEM_ERR_INVALID_ARG, "opts.fill_idle_sms must be 0 or 1");
     if (o->warm_history < 0 || o->warm_history > 1)
         return fail(NPFEM_ERR_INVALID_ARG, "opts.warm_history must be 0 or 1");
-    if (o->precision == NPFEM_PREC_TF32)
-        return fail(NPFEM_ERR_INVALID_ARG,
-                    "NPFEM_PREC_TF32 is not available: a TF32 row block of A^-1 does not fit in tensor memory; "
-                    "use NPFEM_PREC_BF16");
     return 0;
 }
 
@@ -252,7 +248,16 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     memset(&a, 0, sizeof(a));
     long long total = 0, state = 0, slot = 0;
     int smem_max = 0;
-    const int budget = h0->smem_optin - kFixedSmem - 1024;
+    // TF32 tensor-core contraction: the A^-1 ring and the B operand sit in front of the
+    // per-cell vectors, and every block holds 16 tensor-memory columns per row tile
+    const bool tf = sizeof(T) == 4 && mode == 0 && h0->precision == NPFEM_PREC_TF32;
+    int tf_kpad = 0, tf_tiles = 0;
+    for (int gi = 0; tf && gi < n_groups; ++gi) {
+        tf_kpad = std::max(tf_kpad, meshes[gi]->tf.kpad);
+        tf_tiles = std::max(tf_tiles, meshes[gi]->tf.rb);
+    }
+    const int tcb = tf ? tf32_smem_bytes(tf_kpad) : 0;
+    const int budget = h0->smem_optin - kFixedSmem - 1024 - tcb;
     for (int gi = 0; gi < n_groups; ++gi) {
         npfem_handle* h = meshes[gi];
         GroupDesc<T>& g = a.g[gi];
@@ -262,7 +267,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
         g.stats_off = stats_offs ? stats_offs[gi] : total;
         g.cells = cells[gi];
         long long sb = 0;
-        place_vectors(&g, h->n_pad, h->nt, h0->opts.lbfgs_m, budget, &sb);
+        place_vectors(&g, h->n_pad, h->nt, h0->opts.lbfgs_m, budget, &sb, tcb);
         slot = std::max(slot, sb);
         smem_max = std::max(smem_max, g.smem_bytes);
         total += cells[gi];
@@ -282,11 +287,25 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     set_solver_params(&a.p, h0->opts);
     a.p.mode = mode;
     a.p.contraction = CONTRACT_SIMT;
+    int tmem_cols = 0;
+    if (tf) {
+        a.p.contraction = CONTRACT_TC_TF32;
+        a.p.refine = h0->opts.refine;
+        a.p.tf_kpad = tf_kpad;
+        tmem_cols = 32;
+        while (tmem_cols < 16 * tf_tiles) tmem_cols <<= 1;
+        if (tmem_cols > 512) return fail(NPFEM_ERR_INVALID_ARG, "TF32 path: mesh too large (more than 32 row tiles)");
+        a.p.tmem_cols = tmem_cols;
+    }
     a.u0 = u0;
     a.hist_in = hist_in;
     a.hist_out = hist_out;
     a.pos_stride = sizeof(T) == 4 && hist_out ? pos_stride : 0;
     a.defer = defer;
+    if (mode == 0 && h0->col_planes) {
+        a.col = reinterpret_cast<const float4*>(h0->col_planes);
+        a.col_w = (T)h0->col_w;
+    }
 
     if (threads <= 0) threads = h0->threads;
     if (sizeof(T) == 8) threads = std::min(threads, 512);
@@ -295,6 +314,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     int per_sm = 1;
     NPFEM_CUDA(cells_per_sm<T>(threads, smem, &per_sm));
     per_sm = std::max(per_sm, 1);
+    if (tf) per_sm = std::min(per_sm, 512 / tmem_cols);  // every resident block gets its tensor memory
     long long grid = std::min<long long>(total, (long long)h0->sm_count * per_sm);
     a.slot_bytes = slot;
     if (slot > 0) {
@@ -318,11 +338,13 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
 // One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
 int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
                  cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out, long long pos_stride,
-                 unsigned int* only)
+                 unsigned int* only, const float* col = nullptr, double col_w = 0.0)
 {
     if (cells == 0) return 0;
     LaunchArgs<float> a;
     memset(&a, 0, sizeof(a));
+    a.col = reinterpret_cast<const float4*>(col);
+    a.col_w = (float)col_w;
     a.u0 = u0;
     a.hist_in = hist_in;
     a.hist_out = hist_out;
@@ -485,7 +507,10 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
                 if (rc) return rc;
                 only = hg->defer;
             }
-            int rc = run_cells_tc(hg, cg, xg, vg, fg, sg, s, u0 ? u0 + soff[g] : nullptr, hin, hout, pos_stride, only);
+            const npfem_handle* hc = meshes[0];
+            const float* colg = hc->col_planes ? hc->col_planes + 4 * (soff[g] / 3) : nullptr;
+            int rc = run_cells_tc(hg, cg, xg, vg, fg, sg, s, u0 ? u0 + soff[g] : nullptr, hin, hout, pos_stride, only,
+                                  colg, hc->col_w);
             if (rc) return rc;
             done[g] = 1;
         }
@@ -850,6 +875,25 @@ int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_
     rc = h->precision == NPFEM_PREC_FP64 ? fill_topo<double>(h, &h->td, ainv_t, minv_t)
                                          : fill_topo<float>(h, &h->tf, ainv_t, minv_t);
     if (rc) return bail(rc);
+    if (h->precision == NPFEM_PREC_TF32) {
+        // TF32 path: A^-1 in chunks of 128 rows x 32 K in the MMA's layout, and L for the
+        // refinement residual
+        const int kpad = (n + 31) & ~31, tiles = (n + 127) / 128;
+        float* atf = h->alloc<float>((size_t)tiles * 128 * kpad, &e);
+        if (e) return bail(e);
+        if (publish_inverse_tf32_tiled(h->ainv64, n, tiles, kpad, atf, 0) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            return bail(fail(NPFEM_ERR_CUDA, "publishing the TF32 A^-1 failed"));
+        h->tf.ainv_lp = atf;
+        h->tf.kpad = kpad;
+        h->tf.rb = tiles;
+        std::vector<float> lval(h->host.L_val.size());
+        for (size_t q = 0; q < lval.size(); ++q) lval[q] = (float)(lscale * h->host.L_val[q]);
+        std::vector<unsigned short> lidx(h->host.L_idx.begin(), h->host.L_idx.end());
+        if ((rc = upload(h, h->host.L_ptr, &h->tf.h_ptr))) return bail(rc);
+        if ((rc = upload(h, lidx, &h->tf.h_idx))) return bail(rc);
+        if ((rc = upload(h, lval, &h->tf.h_val))) return bail(rc);
+    }
     if (h->precision == NPFEM_PREC_BF16) {
         // tensor-core path: BF16 A^-1 in 128-row blocks with K padded to 16, and L for
         // the refinement residual

@@ -116,6 +116,11 @@ struct CellShared {
     unsigned long long mbar; // tensor-core path: MMA completion barrier
     unsigned need[16];       // tensor-core path: request flags of the cluster's blocks
     unsigned taddr;          // tensor-core path: tensor-memory base address
+    // TF32 contraction (SIMT kernel): per stage of the streamed A^-1 ring, "chunk landed"
+    // and "MMAs done reading it" barriers, and each stage's uses so far (phase parity)
+    unsigned long long tfull[2], tfree[2];
+    unsigned tuse[2];
+    int tfail;               // a bounded wait gave up: later contractions are skipped
     int bad;
     int accept;
     int push;
@@ -354,6 +359,36 @@ __device__ __forceinline__ T* vec_ptr(const GroupDesc<T>& gd, unsigned char* sme
 {
     const int l = gd.loc[v];
     return l >= 0 ? reinterpret_cast<T*>(smem + kFixedSmem + l) : reinterpret_cast<T*>(slot + (-(long long)l - 1));
+}
+
+// A_k (a third of the incident triangle areas) and the unit area-weighted normal of
+// vertex i of a cell whose FP32 SoA positions start at xc (immersed-boundary forces,
+// collision planes).
+__device__ __forceinline__ void vertex_area_normal(const TopoDev<float>& tp, const float* xc, int i, float* A, float n[3])
+{
+    const int n_ = tp.n;
+    float N[3] = {0.f, 0.f, 0.f}, S = 0.f;
+    const int b0 = __ldg(&tp.inc_ptr[i]), b1 = __ldg(&tp.inc_ptr[i + 1]);
+    for (int q = b0; q < b1; ++q) {
+        const unsigned e = __ldg(&tp.inc_idx[q]);
+        const ushort4 tv = __ldg(&tp.tri[e >> 2]);
+        const int p0 = tv.x, p1 = tv.y, p2 = tv.z;
+        float e1[3], e2[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float x0 = xc[c * n_ + p0];
+            e1[c] = xc[c * n_ + p1] - x0;
+            e2[c] = xc[c * n_ + p2] - x0;
+        }
+        const float cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) N[c] += 0.5f * cr[c];
+        S += sqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    }
+    *A = S * (1.f / 6.f);
+    const float inv = rsqrtf(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n[c] = N[c] * inv;
 }
 
 }  // namespace npfem

@@ -134,7 +134,34 @@ __global__ void publish_bf16_blocked(const double* A, int n, int rows_pad, int k
     }
 }
 
+// Element (row i, column k) of A^-1 at its place in the TF32 chunks: chunk (tile, c) of
+// 128 rows x 32 K holds 16 x 8 core matrices of 8 rows x 4 elements (128 bytes), K-adjacent
+// core matrices 128 bytes apart, row groups 1024 bytes apart.
+__global__ void publish_tf32_tiled(const double* A, int n, int tiles, int kpad, float* out)
+{
+    const int nch = kpad / 32;
+    const size_t total = (size_t)tiles * 128 * kpad;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q / kpad), k = (int)(q % kpad);
+        const int t = i >> 7, r = i & 127, c = k >> 5, kk = k & 31;
+        double v = (i < n && k < n) ? A[(size_t)i * n + k] : 0.0;
+        float f = (float)v;
+        unsigned u;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(f));
+        const size_t chunk = (size_t)t * nch + c;
+        const size_t off = chunk * (128 * 32) + (size_t)(((r >> 3) * 8 + (kk >> 2)) * 32 + (r & 7) * 4 + (kk & 3));
+        out[off] = __uint_as_float(u);
+    }
+}
+
 }  // namespace
+
+cudaError_t publish_inverse_tf32_tiled(const double* A, int n, int tiles, int kpad, float* out, cudaStream_t s)
+{
+    publish_tf32_tiled<<<1024, 256, 0, s>>>(A, n, tiles, kpad, out);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t publish_inverse_bf16_blocked(const double* A, int n, int rows_pad, int kpad, void* out, cudaStream_t s)
 {

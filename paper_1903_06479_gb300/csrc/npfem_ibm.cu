@@ -25,6 +25,7 @@
 #include <cstring>
 #include <string>
 
+#include "npfem_device.cuh"
 #include "npfem_internal.h"
 
 namespace npfem {
@@ -108,35 +109,6 @@ __device__ __forceinline__ const IbmGroup& locate(const IbmArgs& a, long long gv
     return G;
 }
 
-// A_k (a third of the incident triangle areas) and the unit area-weighted normal of
-// vertex i of a cell whose SoA positions start at xc.
-__device__ __forceinline__ void area_normal(const TopoDev<float>& tp, const float* xc, int i, float* A, float n[3])
-{
-    const int n_ = tp.n;
-    float N[3] = {0.f, 0.f, 0.f}, S = 0.f;
-    const int b0 = __ldg(&tp.inc_ptr[i]), b1 = __ldg(&tp.inc_ptr[i + 1]);
-    for (int q = b0; q < b1; ++q) {
-        const unsigned e = __ldg(&tp.inc_idx[q]);
-        const ushort4 tv = __ldg(&tp.tri[e >> 2]);
-        const int p0 = tv.x, p1 = tv.y, p2 = tv.z;
-        float e1[3], e2[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float x0 = xc[c * n_ + p0];
-            e1[c] = xc[c * n_ + p1] - x0;
-            e2[c] = xc[c * n_ + p2] - x0;
-        }
-        const float cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) N[c] += 0.5f * cr[c];
-        S += sqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-    }
-    *A = S * (1.f / 6.f);
-    const float inv = rsqrtf(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) n[c] = N[c] * inv;
-}
-
 __device__ __forceinline__ bool node_in(const LatDev& L, int i, int j, int k)
 {
     return (unsigned)i < (unsigned)L.nx && (unsigned)j < (unsigned)L.ny && (unsigned)k < (unsigned)L.nz;
@@ -160,7 +132,7 @@ __global__ void __launch_bounds__(256) ibm_forces_kernel(const __grid_constant__
         const long long so = G.state_off + cell * 3LL * n;
         const float* xc = a.x + so;
         float A, nv[3];
-        area_normal(G.topo, xc, i, &A, nv);
+        vertex_area_normal(G.topo, xc, i, &A, nv);
         Stencil s;
         make_stencil(L, xc[i], xc[n + i], xc[2 * n + i], s);
         float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wsum = 0.f, dbest = -1.f;
@@ -250,7 +222,7 @@ __global__ void __launch_bounds__(256) ibm_forcing_kernel(const __grid_constant_
         if (a.phase == 1) {
             // Step 1: spread f_k with weight A_k dx / dx^3 per unit stencil weight
             float A, nv[3];
-            area_normal(G.topo, xc, i, &A, nv);
+            vertex_area_normal(G.topo, xc, i, &A, nv);
             const float sc = A / (L.dx * L.dx);
             const float f[3] = {sc * o[i], sc * o[n + i], sc * o[2 * n + i]};
             for (int c = 0; c < 4; ++c)

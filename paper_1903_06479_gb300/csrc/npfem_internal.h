@@ -66,11 +66,12 @@ struct TopoDev {
     const unsigned short* l_idx;
     const T* l_val;
     T beta_h;
-    const void* ainv_lp;         // A^-1 for the tensor-core contraction (bf16 or tf32-rounded fp32)
+    const void* ainv_lp;         // A^-1 for the tensor-core contraction: BF16 row blocks, or TF32 chunks
+                                 // of 128 rows x 32 K in the MMA's core-matrix layout
     const int* h_ptr;            // L (CSR, fp32) for the refinement residual q - H~ r
     const unsigned short* h_idx;
     const float* h_val;
-    int kpad, rb;                // tensor-core path: K padded to 16, row blocks of 128
+    int kpad, rb;                // tensor-core path: K padded (16 BF16, 32 TF32), row blocks of 128
     const T* rest_c;             // [3][n] rest positions about the rest centre of mass
     const float* mlp;            // learned warm start: packed parameters, weights rounded to BF16 (or null)
     int ws_mode;                 // 0 none, 1 learned first iterate, 2 learned iterate kept only if g is lower
@@ -101,6 +102,8 @@ struct SolverParams {
     int contraction;  // Contraction
     int cluster;      // tensor-core path: blocks per cluster (= row blocks of A^-1)
     int refine;       // tensor-core path: refinement sweeps (0 or 1)
+    int tmem_cols;    // TF32 path: tensor-memory columns each block allocates
+    int tf_kpad;      // TF32 path: the largest padded K of the launch's groups (B operand size)
 };
 
 inline void set_solver_params(SolverParams* p, const npfem_opts& o)
@@ -147,6 +150,11 @@ struct LaunchArgs {
     const unsigned int* only;
     unsigned int* need;
     double* parts;     // eval mode: 8 doubles per cell
+    // collision planes (Sec. 3.3): per vertex of the call (index = element offset / 3) the
+    // unit normal of the neighbouring body and the plane's offset relative to the
+    // cell's vertex 0; zero normal = none.  Null when the call has no collisions.
+    const float4* col;
+    T col_w;
     npfem_cell_stats* stats;
     char* scratch;     // per-CTA global slots for vectors that do not fit in smem
     long long slot_bytes;
@@ -196,6 +204,9 @@ template <typename T>
 cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s);
 template <typename T>
 cudaError_t set_cell_kernel_smem(int bytes);
+// A^-1 in TF32 (round to nearest) as [row tile][K chunk] blocks of 128 rows x 32 K, each
+// in the no-swizzle K-major core-matrix layout the TF32 MMA reads (16 KB per chunk).
+cudaError_t publish_inverse_tf32_tiled(const double* A, int n, int tiles, int kpad, float* out, cudaStream_t s);
 // Resident SIMT blocks per SM at this block size and dynamic shared memory.
 template <typename T>
 cudaError_t cells_per_sm(int block, int smem, int* n);
@@ -212,6 +223,8 @@ cudaError_t launch_ws_increments(const npfem_handle* h, int n_cells, const float
 // 32-column accumulator within 512 TMEM columns, and at most 8 blocks per cluster.
 constexpr int kTcMaxVerts = 960;
 constexpr int kTcThreads = 512;  // block size of the cluster kernel
+// TF32 path: shared memory for the two-stage A^-1 ring and the B operand (8 x kpad TF32).
+inline int tf32_smem_bytes(int kpad) { return ((2 * 128 * 32 * 4 + 8 * kpad * 4) + 1023) & ~1023; }
 
 // Records msg as the calling thread's last error and returns code (npfem_api.cu).
 int set_error(int code, const std::string& msg);
@@ -307,6 +320,12 @@ struct npfem_handle {
     void* hf = nullptr;
     npfem_cell_stats* hstats = nullptr;
     size_t host_cells = 0;
+    // collisions: planes installed by npfem_set_collisions for the calls through this
+    // handle, and the hash table of npfem_collision_detect
+    const float* col_planes = nullptr;
+    double col_w = 0.0;
+    unsigned* col_table = nullptr;
+    size_t col_table_len = 0;
     // resident clusters of the tensor-core kernel at tc_smem bytes (queried once)
     int tc_max_clusters = 0, tc_smem = -1;
     // side stream and fork/join events of the idle-SM SIMT launch (tensor-core path)
@@ -347,6 +366,9 @@ struct npfem_handle {
         if (defer) cudaFree(defer);
         defer = nullptr;
         defer_len = 0;
+        if (col_table) cudaFree(col_table);
+        col_table = nullptr;
+        col_table_len = 0;
         if (hx) cudaFree(hx);
         if (hv) cudaFree(hv);
         if (hf) cudaFree(hf);

@@ -101,7 +101,7 @@ __device__ __forceinline__ void store_corners(const TopoDev<T>& tp, T* TRI, int 
 // Vn is ignored.
 template <typename T, bool kFirst = false>
 __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T* UY, T* Gout, T* GC, T* TRI, T* WR,
-                         Pair<T> Vn, unsigned char* smem)
+                         Pair<T> Vn, unsigned char* smem, const float4* colp = nullptr, T wcol = T(0))
 {
     const int n = tp.n, np = tp.n_pad, tid = threadIdx.x, NT = blockDim.x;
     CellShared<T>* sh = cell_shared<T>(smem);
@@ -366,7 +366,7 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
 
     // ---- pass 3: bending gather, volume and inertia (M~ = (1 + h alpha_D) M + h beta_D L), residual
     const T ms = tp.inertia_scale * tp.inv_h2, h2 = tp.h * tp.h;
-    Acc<T> ci[1];            // inertia energy
+    Acc<T> ci[2];            // inertia energy, collision energy
     T pr[1] = {T(0)};        // sum_i (h^2 |grad_i| / m_i)^2
     for (int i = tid; i < n; i += NT) {
         const T m = __ldg(&tp.mass[i]);
@@ -408,11 +408,28 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
 #pragma unroll
             for (int c = 0; c < 3; ++c) lb[c] *= tp.beta_h;
         }
+        // collision (Sec. 3.3): while the vertex lies behind its neighbour's tangent plane
+        // (d > 0), (w_col/2) d^2 with gradient -w_col d n; re-tested at every evaluation
+        T gcol[3] = {T(0), T(0), T(0)};
+        if (colp) {
+            const float4 pl = colp[i];
+            if (pl.x != 0.f || pl.y != 0.f || pl.z != 0.f) {
+                const T d = T(pl.w) - (T(pl.x) * (XN[i] + U[i]) + T(pl.y) * (XN[np + i] + U[np + i]) +
+                                       T(pl.z) * (XN[2 * np + i] + U[2 * np + i]));
+                if (d > T(0)) {
+                    const T wd = wcol * d;
+                    gcol[0] = -wd * T(pl.x);
+                    gcol[1] = -wd * T(pl.y);
+                    gcol[2] = -wd * T(pl.z);
+                    ci[1].add(T(0.5) * wd * d);
+                }
+            }
+        }
         T g2 = T(0), ei = T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T du = U[c * np + i] - UY[c * np + i];
-            const T gv = Gout[c * np + i] + gb[c] + volc * GC[c * np + i] + m * ms * du + lb[c];
+            const T gv = Gout[c * np + i] + gb[c] + volc * GC[c * np + i] + m * ms * du + lb[c] + gcol[c];
             Gout[c * np + i] = gv;
             ei += T(0.5) * (m * ms * du + lb[c]) * du;
             g2 += gv * gv;
@@ -422,10 +439,11 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
     }
     const T inv_n = T(1) / T(n), inv_lbar = tp.inv_lbar;
     const T uT = T(Unit<T>::u);
-    block_reduce_cp<T, 1, 1>(ci, pr, smem, [=](CellShared<T>* s) {
+    block_reduce_cp<T, 2, 1>(ci, pr, smem, [=](CellShared<T>* s) {
         s->Ein = {s->out[0], s->outlo[0]};
-        s->E = pair_add(pair_add(pair_add(pair_add(s->Ein, s->Earea), s->Esk), s->Ebend), s->Evol);
-        const T res = sqrt(s->out[1] * inv_n) * inv_lbar;
+        s->E = pair_add(pair_add(pair_add(pair_add(pair_add(s->Ein, s->Earea), s->Esk), s->Ebend), s->Evol),
+                        Pair<T>{s->out[1], s->outlo[1]});
+        const T res = sqrt(s->out[2] * inv_n) * inv_lbar;
         s->res = res;
         s->noise = T(4) * uT * (s->noise + T(2) * s->Ein.hi);
         // non-finite energy or residual marks the evaluation bad
@@ -541,6 +559,294 @@ __device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch
     }
 }
 
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cta_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t map_rank(uint32_t local, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_remote_v4(uint32_t addr, uint4 v)
+{
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_remote_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_remote_u32(uint32_t addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const unsigned short l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const unsigned short h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return ((uint32_t)h << 16) | l;
+}
+
+// byte offset of B element (row nrow, column k) in the no-swizzle K-major layout:
+// 8 x 8 core matrices of 128 bytes, K-adjacent core matrices 128 bytes apart
+// (leading byte offset), row groups (Kpad / 8) * 128 bytes apart (stride byte offset)
+__device__ __forceinline__ uint32_t b_offset(int nrow, int k, int kpad)
+{
+    return (uint32_t)(((nrow >> 3) * (kpad >> 3) + (k >> 3)) * 128 + (nrow & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; no swizzle, base offset 0
+    return d;
+}
+
+template <int NCOL>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[NCOL])
+{
+    uint32_t r[NCOL];
+    if constexpr (NCOL == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+            "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------------
+// TF32 tensor-core contraction inside the persistent SIMT kernel (NPFEM_PREC_TF32).
+// A TF32 row block of A^-1 (128 rows x K, one 32-bit tensor-memory column per K
+// element) does not fit the 512 tensor-memory columns for K = 656, so A^-1 is not kept
+// resident as in the BF16 cluster kernel: every block streams it from L2 in chunks of
+// 128 rows x 32 K (16 KB, laid out in global memory as the MMA's no-swizzle K-major
+// core matrices, one cp.async.bulk each) through a two-stage shared-memory ring, and
+// one thread issues tcgen05.mma.kind::tf32 (M 128, N 16, K 8) per 8 K into tensor
+// memory (16 FP32 columns per row tile).  B is q in TF32: one 8-row group of core
+// matrices (rows 0-2 the three coordinates, rows 3-7 zero) read for both row groups of
+// N = 16 (stride byte offset 0), so columns 8-15 repeat 0-7 and are not read.
+// Blocks work independently: no cluster, no rounds.
+// ---------------------------------------------------------------------------------
+namespace tf32 {
+
+constexpr int kChunkK = 32;
+constexpr int kChunkBytes = 128 * kChunkK * 4;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ float round_tf32(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ bool wait_parity(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (unsigned it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(tc::smem_addr(bar)), "r"(parity));
+    }
+    return done != 0;
+}
+
+// Copies chunk q of the tiled A^-1 into ring stage q & 1.
+__device__ __forceinline__ void load_chunk(const unsigned char* gsrc, unsigned char* stage, unsigned long long* full)
+{
+    const uint32_t bar = tc::smem_addr(full);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)kChunkBytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_addr(stage)),
+                 "l"(gsrc), "r"((uint32_t)kChunkBytes), "r"(bar)
+                 : "memory");
+}
+
+// Set-up at kernel start (all threads): barriers, zero B operand, tensor memory.
+__device__ void setup(int kpad, unsigned char* tcs, CellShared<float>* sh, uint32_t ncols)
+{
+    const int tid = threadIdx.x;
+    unsigned char* bops = tcs + 2 * kChunkBytes;
+    for (int q = tid; q < kpad * 8; q += blockDim.x) reinterpret_cast<float*>(bops)[q] = 0.f;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&sh->tfull[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&sh->tfree[s])));
+            sh->tuse[s] = 0u;
+        }
+        sh->tfail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_addr(&sh->taddr)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ void teardown(CellShared<float>* sh, uint32_t ncols)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sh->taddr), "r"(ncols));
+}
+
+// R = A^-1 Q (three rows of n_pad) with A^-1 in TF32, FP32 accumulation.
+__device__ void contract(const TopoDev<float>& tp, const float* Q, float* R, unsigned char* tcs, CellShared<float>* sh,
+                         unsigned int* err)
+{
+    const int n = tp.n, np = tp.n_pad, kpad = tp.kpad, tid = threadIdx.x, NT = blockDim.x;
+    const int nch = kpad / kChunkK, tiles = tp.rb, total = tiles * nch;
+    unsigned char* bops = tcs + 2 * kChunkBytes;
+    // q in TF32 as B: element (row c, k) of the single row group of core matrices
+    for (int e = tid; e < 3 * kpad; e += NT) {
+        const int c = e / kpad, k = e - c * kpad;
+        const float v = k < n ? Q[c * np + k] : 0.f;
+        *reinterpret_cast<float*>(bops + (k >> 2) * 128 + c * 16 + (k & 3) * 4) = round_tf32(v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const uint32_t tbase = sh->taddr;
+    if (tid == 0 && !sh->tfail) {
+        const unsigned char* gA = static_cast<const unsigned char*>(tp.ainv_lp);
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t sbase = tc::smem_addr(tcs), bbase = tc::smem_addr(bops);
+        uint32_t use[2] = {sh->tuse[0], sh->tuse[1]};
+        bool ok = true;
+        load_chunk(gA, tcs, &sh->tfull[0]);
+        if (total > 1) load_chunk(gA + kChunkBytes, tcs + kChunkBytes, &sh->tfull[1]);
+        for (int q = 0; q < total && ok; ++q) {
+            const int s = q & 1, t = q / nch, c = q - t * nch;
+            const uint32_t u = use[s] + (uint32_t)(q >> 1);
+            ok = wait_parity(&sh->tfull[s], u & 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < kChunkK / 8; ++ks) {
+                const uint64_t ad = tc::smem_desc(sbase + (uint32_t)(s * kChunkBytes + ks * 256), 128u, 1024u);
+                const uint64_t bd = tc::smem_desc(bbase + (uint32_t)((c * (kChunkK / 8) + ks) * 256), 128u, 0u);
+                const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tbase + (uint32_t)(16 * t)),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc::smem_addr(&sh->tfree[s])));
+            if (q + 2 < total) {
+                // the stage is refilled once its MMAs have read it
+                ok = wait_parity(&sh->tfree[s], u & 1u);
+                if (ok) load_chunk(gA + (size_t)(q + 2) * kChunkBytes, tcs + s * kChunkBytes, &sh->tfull[s]);
+            }
+        }
+        // the last use of each stage: its MMAs complete in order, after every earlier one
+        for (int q = total - 2; q < total && ok; ++q) {
+            if (q < 0) continue;
+            const int s = q & 1;
+            ok = wait_parity(&sh->tfree[s], (use[s] + (uint32_t)(q >> 1)) & 1u);
+        }
+        sh->tuse[0] = use[0] + (uint32_t)((total + 1) / 2);
+        sh->tuse[1] = use[1] + (uint32_t)(total / 2);
+        if (!ok) {
+            sh->tfail = 1;
+            atomicExch(err, 1u);  // reported to the host; results invalid
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // D: warp w reads the lanes of its quadrant (w % 4) of row tiles w / 4, w / 4 + NW / 4, ...
+    const int warp = tid >> 5, lane = tid & 31, nwq = (NT >> 5) >> 2;
+    if ((warp >> 2) < nwq) {
+        const int quad = warp & 3;
+        for (int t = warp >> 2; t < tiles; t += nwq) {
+            float dv[16];
+            tc::tmem_ld<16>(tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)(16 * t), dv);
+            const int row = 128 * t + 32 * quad + lane;
+            if (row < np) {
+                const bool live = row < n && !sh->tfail;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) R[c * np + row] = live ? dv[c] : 0.f;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+}
+
+}  // namespace tf32
+
+// Refinement residual e = q - H~ r (H~ = ms M + (1 + beta_D/h) L, L sparse FP32), one row
+// (three components) per thread, into tmp (3 x n_pad; zero padding).
+template <typename T>
+__device__ void refine_residual(const TopoDev<T>& tp, const T* src, const T* R, T* tmp)
+{
+    const int n = tp.n, np = tp.n_pad, tid = threadIdx.x, NT = blockDim.x;
+    const T ms = tp.inertia_scale * tp.inv_h2;
+    for (int i = tid; i < np; i += NT) {
+        T e0 = T(0), e1 = T(0), e2 = T(0);
+        if (i < n) {
+            const T mm = ms * __ldg(&tp.mass[i]);
+            T h0 = mm * R[i], h1 = mm * R[np + i], h2 = mm * R[2 * np + i];
+            const int b0 = __ldg(&tp.h_ptr[i]), b1 = __ldg(&tp.h_ptr[i + 1]);
+            for (int p = b0; p < b1; ++p) {
+                const T lv = __ldg(&tp.h_val[p]);
+                const int j = __ldg(&tp.h_idx[p]);
+                h0 += lv * R[j];
+                h1 += lv * R[np + j];
+                h2 += lv * R[2 * np + j];
+            }
+            e0 = src[i] - h0;
+            e1 = src[np + i] - h1;
+            e2 = src[2 * np + i] - h2;
+        }
+        tmp[i] = e0;
+        tmp[np + i] = e1;
+        tmp[2 * np + i] = e2;
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------
 // One cell's quasi-Newton solve, split into the phases that both kernels drive.
 // All threads of the block call every method (control flow is block-uniform).
@@ -558,6 +864,8 @@ struct CellSolver {
     Pair<T> E, Vlast, Vn;
     T noiseE, res, gdv;
     bool nonfinite;
+    const float4* colp;  // this cell's collision planes, or null
+    T wcol;
 
     __device__ const TopoDev<T>& tp() const { return gd->topo; }
     __device__ T* hist(int v) const { return vec_ptr(*gd, smem, slot, v); }
@@ -591,6 +899,8 @@ struct CellSolver {
         const int n = T_.n, np = T_.n_pad, N3 = 3 * np, tid = threadIdx.x, NT = blockDim.x;
         item = it;
         so = gd->state_off + cell * 3LL * n;
+        colp = a->col ? a->col + so / 3 : nullptr;
+        wcol = a->col_w;
         const T h = T_.h, inv_ms = T(1) / T_.inertia_scale;
         const bool eval_mode = a->p.mode == 1;
         const bool hist = !eval_mode && a->hist_in;
@@ -706,12 +1016,12 @@ struct CellSolver {
             // keep the learned guess only if it lowers g: evaluate at y (trial buffers) first
             for (int e = tid; e < N3; e += NT) ut[e] = UYv[e];
             __syncthreads();
-            evaluate<T, true>(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, Pair<T>{T(0), T(0)}, smem);
+            evaluate<T, true>(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, Pair<T>{T(0), T(0)}, smem, colp, wcol);
             Vn = sh->Vn;
             const Pair<T> Ey = sh->E, Vy = sh->V;
             const T ny = sh->noise, ry = sh->res;
             const bool by = sh->bad;
-            evaluate<T, false>(T_, XN, u, UYv, g, GCv, TRIv, WRv, Vn, smem);
+            evaluate<T, false>(T_, XN, u, UYv, g, GCv, TRIv, WRv, Vn, smem, colp, wcol);
             evals = 2;
             if (!(pair_diff(sh->E, Ey) <= T(0)) && !by) {
                 T* t1 = u; u = ut; ut = t1;
@@ -726,7 +1036,7 @@ struct CellSolver {
                 __syncthreads();
             }
         } else {
-            evaluate<T, true>(T_, XN, u, UYv, g, GCv, TRIv, WRv, Pair<T>{T(0), T(0)}, smem);
+            evaluate<T, true>(T_, XN, u, UYv, g, GCv, TRIv, WRv, Pair<T>{T(0), T(0)}, smem, colp, wcol);
             Vn = sh->Vn;
         }
         iters = 0;
@@ -917,7 +1227,7 @@ struct CellSolver {
                 st4(ut + e, uv);
             }
             __syncthreads();
-            evaluate(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, Vn, smem);
+            evaluate(T_, XN, ut, UYv, gt, GCv, TRIv, WRv, Vn, smem, colp, wcol);
             ++evals;
             if (tid == 0) {
                 const bool ok = !sh->bad && pair_diff(sh->E, E) <= c1 * alpha * gdv + anoise * (sh->noise + noiseE);
@@ -1215,11 +1525,37 @@ __device__ __forceinline__ void release_counters(unsigned int* work, int total_b
     }
 }
 
+// R = H0 Q for the SIMT kernel: FP32/FP64 on the SIMT pipes, or TF32 tensor cores
+// (with the optional refinement sweep r += A^-1 (q - H~ r), its correction in `tmp2`).
+template <typename T>
+__device__ __forceinline__ void contract_any(const LaunchArgs<T>& a, const TopoDev<T>& tp, const T* Q, T* R,
+                                             CellSolver<T>& S, unsigned char* smem)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (a.p.contraction == CONTRACT_TC_TF32) {
+            CellShared<float>* sh = cell_shared<float>(smem);
+            tf32::contract(tp, Q, R, smem + kFixedSmem, sh, a.work + 2);
+            if (a.p.refine) {
+                refine_residual(tp, Q, R, S.WRv);
+                tf32::contract(tp, S.WRv, S.ut, smem + kFixedSmem, sh, a.work + 2);
+                for (int e = threadIdx.x; e < 3 * tp.n_pad; e += blockDim.x) R[e] += S.ut[e];
+                __syncthreads();
+            }
+            return;
+        }
+    }
+    contract_simt(tp, Q, R, S.TRIv);
+}
+
 template <typename T, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) cell_kernel(const __grid_constant__ LaunchArgs<T> a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     CellSolver<T> S;
+    if constexpr (sizeof(T) == 4) {
+        if (a.p.contraction == CONTRACT_TC_TF32)
+            tf32::setup(a.p.tf_kpad, smem + kFixedSmem, cell_shared<float>(smem), (uint32_t)a.p.tmem_cols);
+    }
     // first-iterate pass: evaluate only while most cells of the last step were accepted
     const bool eval_first = a.defer && 2ll * (long long)a.defer[2] <= a.total_cells;
     for (;;) {
@@ -1244,17 +1580,20 @@ __global__ void __launch_bounds__(MAXT, 1) cell_kernel(const __grid_constant__ L
         const TopoDev<T>& tp = a.g[gi].topo;
         while (S.wants_direction()) {
             S.first_loop();
-            contract_simt(tp, S.Dv, S.GCv, S.TRIv);  // r = H0 q
+            contract_any(a, tp, S.Dv, S.GCv, S, smem);  // r = H0 q
             S.second_loop();
             if (!S.descent()) {
                 // not a descent direction: drop the history, d = -H~^-1 g
                 S.count = 0;
-                contract_simt(tp, S.g, S.GCv, S.TRIv);
+                contract_any(a, tp, S.g, S.GCv, S, smem);
                 S.negate_direction();
             }
             if (!S.line_search_update()) break;
         }
         S.finish();
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (a.p.contraction == CONTRACT_TC_TF32) tf32::teardown(cell_shared<float>(smem), (uint32_t)a.p.tmem_cols);
     }
     release_counters(a.work, a.total_blocks);
 }
@@ -1274,97 +1613,6 @@ __global__ void __launch_bounds__(MAXT, 1) cell_kernel(const __grid_constant__ L
 // Blocks without work still take part until every block of the cluster is idle, so
 // all blocks pass the same sequence of cluster barriers.
 // ---------------------------------------------------------------------------------
-namespace tc {
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t cta_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ uint32_t map_rank(uint32_t local, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ void st_remote_v4(uint32_t addr, uint4 v)
-{
-    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
-                 "r"(v.w)
-                 : "memory");
-}
-
-__device__ __forceinline__ void st_remote_f32(uint32_t addr, float v)
-{
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_remote_u32(uint32_t addr, uint32_t v)
-{
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
-{
-    const unsigned short l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
-    const unsigned short h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
-    return ((uint32_t)h << 16) | l;
-}
-
-// byte offset of B element (row nrow, column k) in the no-swizzle K-major layout:
-// 8 x 8 core matrices of 128 bytes, K-adjacent core matrices 128 bytes apart
-// (leading byte offset), row groups (Kpad / 8) * 128 bytes apart (stride byte offset)
-__device__ __forceinline__ uint32_t b_offset(int nrow, int k, int kpad)
-{
-    return (uint32_t)(((nrow >> 3) * (kpad >> 3) + (k >> 3)) * 128 + (nrow & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; no swizzle, base offset 0
-    return d;
-}
-
-template <int NCOL>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[NCOL])
-{
-    uint32_t r[NCOL];
-    if constexpr (NCOL == 32) {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
-            "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr));
-    } else {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < NCOL; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-}  // namespace tc
 
 // Writes BF16(src) (3 rows of the cell, zero beyond n) into rows 3 rank + c of the B
 // operand of every block in the cluster.  If with_residual, writes instead the
@@ -1378,30 +1626,7 @@ __device__ void tc_post(const TopoDev<T>& tp, const T* src, const T* R, bool wit
     const int chunks = 3 * (kpad >> 3);
     const uint32_t local = tc::smem_addr(bbuf);
     if (with_residual) {
-        // e = src - H~ R, one row (three components) per thread
-        const T ms = tp.inertia_scale * tp.inv_h2;
-        for (int i = tid; i < np; i += NT) {
-            T e0 = T(0), e1 = T(0), e2 = T(0);
-            if (i < n) {
-                const T mm = ms * __ldg(&tp.mass[i]);
-                T h0 = mm * R[i], h1 = mm * R[np + i], h2 = mm * R[2 * np + i];
-                const int b0 = __ldg(&tp.h_ptr[i]), b1 = __ldg(&tp.h_ptr[i + 1]);
-                for (int p = b0; p < b1; ++p) {
-                    const T lv = __ldg(&tp.h_val[p]);
-                    const int j = __ldg(&tp.h_idx[p]);
-                    h0 += lv * R[j];
-                    h1 += lv * R[np + j];
-                    h2 += lv * R[2 * np + j];
-                }
-                e0 = src[i] - h0;
-                e1 = src[np + i] - h1;
-                e2 = src[2 * np + i] - h2;
-            }
-            tmp[i] = e0;
-            tmp[np + i] = e1;
-            tmp[2 * np + i] = e2;
-        }
-        __syncthreads();
+        refine_residual(tp, src, R, tmp);
         src = tmp;
     }
     for (int q = tid; q < chunks; q += NT) {

@@ -107,6 +107,10 @@ int run_static(npfem_handle* const* meshes, const std::vector<int>& sel, const i
     set_solver_params(&a.p, h0->opts);
     a.p.mode = 0;
     a.p.contraction = CONTRACT_SIMT;
+    if (meshes[0]->col_planes) {
+        a.col = reinterpret_cast<const float4*>(meshes[0]->col_planes);
+        a.col_w = (T)meshes[0]->col_w;
+    }
 
     const int smem = kFixedSmem + smem_max;
     cudaError_t e = set_cell_kernel_smem<T>(smem);

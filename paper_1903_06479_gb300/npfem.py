@@ -63,7 +63,8 @@ EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", 
            "npfem_mlp_predict", "npfem_set_warmstart", "npfem_ws_guess", "npfem_launch_count",
            "npfem_kernel_timing", "npfem_kernel_times", "npfem_graph_create", "npfem_graph_launch",
            "npfem_graph_destroy", "npfem_kernel_time_last", "npfem_autotune", "npfem_get_tuning",
-           "npfem_flag_wait_timeout", "npfem_ibm_forces", "npfem_ibm_interpolate", "npfem_ibm_forcing")
+           "npfem_flag_wait_timeout", "npfem_ibm_forces", "npfem_ibm_interpolate", "npfem_ibm_forcing",
+           "npfem_collision_detect", "npfem_set_collisions")
 
 
 def lib_path() -> str:
@@ -99,6 +100,8 @@ def lib():
         L.npfem_get_rest_info.argtypes = [vp, vp, vp]
         L.npfem_check_device.argtypes = [vp]
         L.npfem_flag_wait_timeout.argtypes = [vp]
+        L.npfem_collision_detect.argtypes = [vp, i32, vp, vp, C.c_double, vp, vp, vp]
+        L.npfem_set_collisions.argtypes = [vp, vp, C.c_double]
         L.npfem_ibm_forces.argtypes = [vp, i32, vp, vp, C.POINTER(Lattice), vp, C.c_double, i32, vp, vp]
         L.npfem_ibm_interpolate.argtypes = [vp, i32, vp, vp, C.POINTER(Lattice), vp, vp, vp]
         L.npfem_ibm_forcing.argtypes = [vp, i32, vp, vp, vp, C.POINTER(Lattice), vp, C.c_double, i32, vp, vp, vp]
@@ -205,6 +208,10 @@ class Handle:
     def check_device(self):
         """Raises NpfemError(-5) if a bounded device wait of a previous step gave up."""
         _check(lib().npfem_check_device(self._h))
+
+    def set_collisions(self, planes, w_col: float):
+        """npfem_set_collisions: collision planes (device) for the steps through this handle."""
+        _check(lib().npfem_set_collisions(self._h, _addr(planes), float(w_col) if planes is not None else 0.0))
 
     def flag_wait_timeout(self):
         """Sets the device-wait flag as a timed-out wait would (tests the reporting path)."""
@@ -336,6 +343,13 @@ def ibm_forcing(handles, cells_per_group, x, u_vertex, lat: Lattice, u_lattice, 
     arr, ng, cells = _groups(handles, cells_per_group)
     _check(lib().npfem_ibm_forcing(arr, ng, cells, _addr(x), _addr(u_vertex), C.byref(lat), _addr(u_lattice),
                                    float(dt_fluid), int(cycles), _addr(f_vertex), _addr(f_lattice), _addr(stream)))
+
+
+def collision_detect(handles, cells_per_group, x, cutoff: float, planes, stats, stream=None):
+    """npfem_collision_detect: per-vertex planes of the nearest vertex of another cell."""
+    arr, ng, cells = _groups(handles, cells_per_group)
+    _check(lib().npfem_collision_detect(arr, ng, cells, _addr(x), float(cutoff), _addr(planes), _addr(stats),
+                                        _addr(stream)))
 
 
 def step_static(handles, cells_per_group, x, v, f, dt: float, stream=None, stats=None):

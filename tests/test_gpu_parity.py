@@ -144,7 +144,7 @@ def test_several_steps_fp32(npfem):
     assert max_rel_disp(xg, xo, m.lbar) <= 5e-5
 
 
-@pytest.mark.parametrize("prec,tune", [("fp32", False), ("bf16", False), ("bf16", True)])
+@pytest.mark.parametrize("prec,tune", [("fp32", False), ("bf16", False), ("bf16", True), ("tf32", False)])
 def test_mixed_resolutions_one_step(npfem, prec, tune):
     """One step over 2562-, 642- and 258-vertex groups: a single persistent SIMT launch
     (FP32), cluster launches for the groups that fit the tensor-core kernel plus a SIMT
@@ -303,10 +303,47 @@ def test_bf16_full_size_sampled(npfem):
     assert max_rel_disp(xg[sample], xo, m.lbar) <= 1e-5 + fp32_store_allowance(p["x"], m.lbar)
 
 
-def test_tf32_is_rejected(npfem):
-    with pytest.raises(npfem.NpfemError) as e:
-        make_handle(npfem, 258, "tf32")
-    assert e.value.code == -1
+@pytest.mark.parametrize("n_verts,cells,refine", [(642, 13, 1), (642, 8, 0), (258, 7, 1), (2562, 2, 0)])
+def test_step_tf32_tensor_core(npfem, n_verts, cells, refine):
+    # TF32 A^-1 streamed through the tensor cores by every SIMT block (2562 vertices: 21
+    # row tiles, 336 accumulator columns)
+    h = make_handle(npfem, n_verts, "tf32", tol=1e-6, refine=refine)
+    m, _, _ = oracle_model(n_verts)
+    p = population32(n_verts, cells, seed=40 + n_verts, forces="shear", noise_pN=0.5)
+    key = ("tc", n_verts, cells)
+    if key not in _ORACLE:
+        _ORACLE[key] = oracle_steps(m, p["x"], p["v"], p["f"], tol=1e-10, max_iter=200)
+    xo, vo, st = _ORACLE[key]
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    h.check_device()
+    assert (sg["status"] == 0).all(), sg
+    assert (sg["residual"] <= 1e-6).all()
+    assert max_rel_disp(xg, xo, m.lbar) <= 1e-5 + fp32_store_allowance(p["x"], m.lbar)
+    assert max_rel_disp(DT * vg, DT * vo, m.lbar) <= 1e-5
+
+
+def test_tf32_iterations_close_to_fp32(npfem):
+    # the TF32 contraction changes the direction by ~2^-11 relative: iteration counts stay
+    # those of the FP32 contraction
+    p = population32(642, 64, seed=50, forces="shear", noise_pN=0.5)
+    out = {}
+    for prec in ("fp32", "tf32"):
+        h = make_handle(npfem, 642, prec, tol=1e-6, warm_history=0)
+        _, _, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+        out[prec] = sg["iterations"].mean()
+    assert out["tf32"] <= out["fp32"] + 0.5, out
+
+
+def test_tf32_full_size_sampled(npfem):
+    h = make_handle(npfem, 642, "tf32", tol=1e-6)
+    m, _, _ = oracle_model(642)
+    p = population32(642, 16384, seed=3, forces="shear", gamma_fixed=1000.0, noise_pN=2.0)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"])
+    h.check_device()
+    assert (sg["status"] == 0).all() and (sg["residual"] <= 1e-6).all()
+    sample = np.random.default_rng(1).choice(16384, 8, replace=False)
+    xo, vo, _ = oracle_steps(m, p["x"][sample], p["v"][sample], p["f"][sample], tol=1e-10, max_iter=200)
+    assert max_rel_disp(xg[sample], xo, m.lbar) <= 1e-5 + fp32_store_allowance(p["x"], m.lbar)
 
 
 def _volumes(x, tris):
@@ -314,7 +351,7 @@ def _volumes(x, tris):
     return np.einsum("cti,cti->ct", a, np.cross(b, c)).sum(1) / 6.0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
 def test_multistep_drift_against_fp64_oracle(npfem, prec):
     """20 steps of 8 cells under N(0, 2 pN) noise plus 1000/s shear: positions and
     volumes against the FP64 oracle (run to 1e-10).  Each step converges to 1e-6 and
