@@ -202,3 +202,22 @@ def to_soa(a: np.ndarray) -> np.ndarray:
 
 def from_soa(a: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.swapaxes(a, -1, -2))
+
+
+def bead_vertices(rest: np.ndarray, patch_um: float = 2.0) -> tuple[np.ndarray, np.ndarray]:
+    """Vertices held by the two optical-tweezers beads of the stretching experiment
+    (Sec. 3.1): those within patch_um of the rest shape's extreme points along x
+    (left, right)."""
+    left = np.where(np.linalg.norm(rest - rest[np.argmin(rest[:, 0])], axis=1) <= patch_um)[0]
+    right = np.where(np.linalg.norm(rest - rest[np.argmax(rest[:, 0])], axis=1) <= patch_um)[0]
+    return left, right
+
+
+def stretch_forces(rest: np.ndarray, force_pN: float, patch_um: float = 2.0) -> np.ndarray:
+    """Equal and opposite total forces +-force_pN along x, spread evenly over each
+    bead's vertices: [n, 3]."""
+    left, right = bead_vertices(rest, patch_um)
+    f = np.zeros_like(rest)
+    f[right, 0] = force_pN / len(right)
+    f[left, 0] = -force_pN / len(left)
+    return f

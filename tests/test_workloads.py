@@ -2,6 +2,7 @@
 (paper_1903_06479_gb300/workloads.py): rigid placements, the shear-traction stand-in
 for the immersed-boundary force (Eq. Fext) and its noise."""
 import numpy as np
+import pytest
 
 from paper_1903_06479_gb300 import workloads as W
 
@@ -72,3 +73,30 @@ def test_soa_round_trip():
     s = W.to_soa(a)
     assert s.shape == (5, 3, 7) and s.flags["C_CONTIGUOUS"]
     assert np.array_equal(W.from_soa(s), a)
+
+
+def test_stretch_forces_balance_and_bead_patches():
+    rest, tris = W.discocyte(258)
+    for F in (0.0, 50.0, 200.0):
+        f = W.stretch_forces(rest, F, 2.0)
+        assert np.abs(f.sum(0)).max() < 1e-12  # equal and opposite
+        left, right = W.bead_vertices(rest, 2.0)
+        assert f[right, 0].sum() == pytest.approx(F) and f[left, 0].sum() == pytest.approx(-F)
+        assert (rest[right, 0] > 0).all() and (rest[left, 0] < 0).all()
+    # torque-free: the patches are mirror images on the x axis
+    assert np.abs(np.cross(rest, W.stretch_forces(rest, 100.0)).sum(0)).max() < 1e-9
+
+
+def test_elongation_index_and_recovery_fit():
+    from paper_1903_06479_gb300 import validation as V
+    lam0, linf = 2.4, 1.0
+    assert V.elongation_index(lam0, lam0, linf) == pytest.approx(1.0)
+    assert V.elongation_index(linf, lam0, linf) == pytest.approx(0.0)
+    t = np.linspace(0, 5000, 40)
+    tc, delta, r2 = V.fit_recovery_time(t, np.exp(-t / 1234.0))
+    assert tc == pytest.approx(1234.0, rel=1e-9) and delta == pytest.approx(1.0) and r2 == pytest.approx(1.0)
+    tc, delta, r2 = V.fit_recovery_time(t, np.exp(-(t / 2500.0) ** 0.7))
+    assert tc == pytest.approx(2500.0, rel=1e-9) and delta == pytest.approx(0.7) and r2 == pytest.approx(1.0)
+    x = np.random.default_rng(0).standard_normal((50, 3))
+    DA, DT = V.diameters(x)
+    assert DA == pytest.approx(np.ptp(x[:, 0])) and DT == pytest.approx(np.ptp(x[:, 1]))
