@@ -1179,6 +1179,62 @@ void or_ws_features(const or_model *m, const double *y, const double *f, double 
     free(d);
 }
 
+/* Temporal network (an addition, not in the paper): along a trajectory the first       */
+/* iterate is y_n + c_{n-1} + R MLP(features), c_k = x_{k+1} - y_k the converged          */
+/* correction of step k, R the best-fit rotation at y_n.  Features of vertex i (9), in    */
+/* the rest frame: the trend R^T (c_{n-1} - c_{n-2}), the force change as a displacement  */
+/* u = R^T h^2 (F_n - F_{n-1}) / m_i, and its cotangent Laplacian over the one-ring.       */
+void or_ws_features_temporal(const or_model *m, const double *y, const double *f, const double *f_prev,
+                             const double *c1, const double *c2, double *feat, double *Rout)
+{
+    int n = m->n;
+    double ycm[3], xcm[3];
+    or_best_rotation(m, y, Rout, ycm, xcm);
+    const double *R = Rout;
+    double *u = (double *)malloc(sizeof(double) * 3 * n);
+    for (int i = 0; i < n; ++i) {
+        double sc = m->h * m->h / m->mass[i];
+        for (int b = 0; b < 3; ++b) {
+            double su = 0.0, st = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                su += R[3 * a + b] * (f[3 * i + a] - f_prev[3 * i + a]);
+                st += R[3 * a + b] * (c1[3 * i + a] - c2[3 * i + a]);
+            }
+            u[3 * i + b] = su * sc;
+            feat[9 * i + b] = st;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double lap[3] = {0, 0, 0};
+        for (int q = m->ring_ptr[i]; q < m->ring_ptr[i + 1]; ++q) {
+            int j = m->ring_idx[q];
+            for (int r = 0; r < 3; ++r) lap[r] += m->ring_c[q] * (u[3 * j + r] - u[3 * i + r]);
+        }
+        for (int b = 0; b < 3; ++b) {
+            feat[9 * i + 3 + b] = u[3 * i + b];
+            feat[9 * i + 6 + b] = lap[b];
+        }
+    }
+    free(u);
+}
+
+/* x1 = y + c_{n-1} + R (s_out * MLP(temporal features)). */
+void or_ws_guess_temporal(const or_model *m, const double *P, const double *x, const double *v, const double *f,
+                          const double *f_prev, const double *c1, const double *c2, double *x1, int bf16)
+{
+    int n = m->n;
+    double *y = (double *)malloc(sizeof(double) * 3 * n), *feat = (double *)malloc(sizeof(double) * 9 * n);
+    double *o = (double *)malloc(sizeof(double) * 3 * n), R[9];
+    or_first_guess(m, x, v, f, y);
+    or_ws_features_temporal(m, y, f, f_prev, c1, c2, feat, R);
+    or_mlp_predict(P, feat, n, o, bf16);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a)
+            x1[3 * i + a] = y[3 * i + a] + c1[3 * i + a] + R[3 * a + 0] * o[3 * i] + R[3 * a + 1] * o[3 * i + 1] +
+                            R[3 * a + 2] * o[3 * i + 2];
+    free(y); free(feat); free(o);
+}
+
 /* Warm-started first guess: x1 = y + R (s_out * MLP(features)). */
 void or_ws_guess(const or_model *m, const double *P, const double *x, const double *v, const double *f, double *x1,
                  int bf16)

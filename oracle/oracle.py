@@ -105,6 +105,8 @@ def lib():
         L.or_step_batch_col.restype = C.c_int
         L.or_step_batch_col.argtypes = [P, C.c_int, C.c_int, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats), C.c_int,
                                         P, C.c_double]
+        L.or_ws_features_temporal.argtypes = [P, dp, dp, dp, dp, dp, dp, dp]
+        L.or_ws_guess_temporal.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
         L.or_step_batch.restype = C.c_int
         L.or_step_batch.argtypes = [P, C.c_int, C.c_int, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats), C.c_int]
         _lib = L
@@ -298,6 +300,19 @@ class Model:
     def ws_guess(self, P, x, v, f, bf16_operands=True):
         x1 = np.zeros((self.n, 3))
         lib().or_ws_guess(self._h, np.ascontiguousarray(P, dtype=np.float64), *(np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, f)), x1, int(bf16_operands))
+        return x1
+
+    def ws_features_temporal(self, y, f, f_prev, c1, c2):
+        """Features of the temporal network at y (trend of the corrections, force change)."""
+        a = [np.ascontiguousarray(t, dtype=np.float64) for t in (y, f, f_prev, c1, c2)]
+        feat = np.zeros((self.n, 9)); R = np.zeros(9)
+        lib().or_ws_features_temporal(self._h, *a, feat, R)
+        return feat, R.reshape(3, 3)
+
+    def ws_guess_temporal(self, P, x, v, f, f_prev, c1, c2, bf16_operands=True):
+        x1 = np.zeros((self.n, 3))
+        a = [np.ascontiguousarray(t, dtype=np.float64) for t in (x, v, f, f_prev, c1, c2)]
+        lib().or_ws_guess_temporal(self._h, np.ascontiguousarray(P, dtype=np.float64), *a, x1, int(bf16_operands))
         return x1
 
     def step_batch(self, x, v, f, opts: Opts | None = None, steps: int = 1, threads: int = 1, col=None, wcol=0.0):

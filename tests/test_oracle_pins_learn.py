@@ -115,3 +115,50 @@ def test_bf16_operand_network_within_rounding_bound():
     err = np.abs(o16 - o64)
     assert np.all(err <= bound), (err / bound).max()
     assert err.max() > 1e-3 * bound.max()
+
+
+# ---------------------------------------------------------------------------------------
+# temporal network: features of the force change and of the corrections' trend
+# ---------------------------------------------------------------------------------------
+def test_temporal_features_vanish_on_a_steady_trajectory(m642):
+    # F_n = F_{n-1} and c_{n-1} = c_{n-2}: nothing changes between steps, every feature is 0
+    rng = np.random.default_rng(40)
+    y = m642.rest + 0.02 * m642.lbar * rng.standard_normal(m642.rest.shape)
+    f = rng.normal(0, 1.0, y.shape)
+    c = 1e-3 * rng.standard_normal(y.shape)
+    feat, _ = m642.ws_features_temporal(y, f, f, c, c)
+    assert np.abs(feat).max() == 0.0
+
+
+def test_temporal_features_closed_forms_and_rotation_invariance(m642):
+    rng = np.random.default_rng(41)
+    y = m642.rest + 0.02 * m642.lbar * rng.standard_normal(m642.rest.shape)
+    M = m642.masses()[:, None]
+    # a force change that is a uniform displacement h^2 dF / m = a: u = R^T a everywhere and
+    # its Laplacian vanishes (the cotangent weights' rows sum to c_ii)
+    a = np.array([0.003, -0.001, 0.002])
+    df = a[None, :] * M / DT ** 2
+    c1, c2 = rng.standard_normal(y.shape) * 1e-3, rng.standard_normal(y.shape) * 1e-3
+    f0 = rng.normal(0, 1.0, y.shape)
+    feat, R = m642.ws_features_temporal(y, f0 + df, f0, c1, c2)
+    assert np.abs(feat[:, 3:6] - (a @ R)[None, :]).max() < 1e-14
+    assert np.abs(feat[:, 6:9]).max() < 1e-10 * np.abs(a).max() / m642.lbar ** 2
+    assert np.abs(feat[:, 0:3] - (c1 - c2) @ R).max() < 1e-15
+    # rigid motion of the whole state rotates nothing in the features
+    Q = W.random_rotations(rng, 1)[0]
+    f1 = rng.normal(0, 1.0, y.shape)
+    fa, Ra = m642.ws_features_temporal(y, f1, f0, c1, c2)
+    fb, Rb = m642.ws_features_temporal(y @ Q.T + 7.0, f1 @ Q.T, f0 @ Q.T, c1 @ Q.T, c2 @ Q.T)
+    assert np.abs(fa - fb).max() < 1e-10 * np.abs(fa).max()
+
+
+def test_temporal_guess_with_zero_output_is_the_temporal_warm_start(m642):
+    P = rand_params(42)
+    P[4800:4995] = 0.0  # W3 and b3
+    p = W.population(642, 1, 43, forces="noise", noise_pN=1.0)
+    rng = np.random.default_rng(44)
+    c1, c2 = 1e-3 * rng.standard_normal(p["x"][0].shape), 1e-3 * rng.standard_normal(p["x"][0].shape)
+    f_prev = p["f"][0] + rng.normal(0, 0.5, p["f"][0].shape)
+    x1 = m642.ws_guess_temporal(P, p["x"][0], p["v"][0], p["f"][0], f_prev, c1, c2)
+    y = m642.first_guess(p["x"][0], p["v"][0], p["f"][0])
+    assert np.abs(x1 - (y + c1)).max() < 1e-15 * np.abs(y).max() + 1e-18
