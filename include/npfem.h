@@ -278,6 +278,37 @@ int npfem_mlp_predict(const float* params, const float* feat, int n, float* out,
    Blocks.  FP32-state handles only.  Errors: INVALID_ARG, OOM, CUDA. */
 int npfem_set_warmstart(npfem_handle* h, const float* params_host, int mode);
 
+/* Temporal network (an addition to the paper's method): along a trajectory stepped
+   with opts.warm_history, the first iterate of step n is
+   y_n + c_{n-1} + R MLP(features) instead of y_n + c_{n-1}, c_k = x_{k+1} - y_k the
+   converged correction of step k (kept by the library) and R the mass-weighted best-fit
+   rotation of the rest shape onto y_n.  Features of vertex i (9, rest frame): the trend
+   R^T (c_{n-1} - c_{n-2}), the force change as a displacement R^T h^2 (F_n - F_{n-1}) / m_i
+   and its cotangent Laplacian over the one-ring; the target is R^T (c_n - c_{n-1}).  The
+   network has the layout and arithmetic of the warm start above.  With a network
+   installed on any group of a call, the trajectory state grows by c_{n-2} and F_{n-1}
+   (24n more bytes per cell).  The iteration still runs to the residual tolerance. */
+
+/* Installs (params_host, 5016 FP32, weights rounded to BF16) or removes (NULL) the
+   temporal network of h; the next step through h restarts its trajectory.  FP32-state
+   handles.  Blocks.  Errors: INVALID_ARG, OOM, CUDA. */
+int npfem_set_warmstart_temporal(npfem_handle* h, const float* params_host);
+
+/* Training data of the temporal network for n_cells cells of h (device SoA FP32): the
+   features at x, v, f with the previous force f_prev and the corrections c1 = c_{n-1},
+   c2 = c_{n-2} into feat ([n_cells * n_verts][9]); with the converged x_next also the
+   target into target ([..][3], or NULL) and c_n = x_next - y_n into c_out (SoA, or
+   NULL).  Errors: INVALID_ARG, CUDA. */
+int npfem_ws_features_temporal(npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
+                               const float* f_prev, const float* c1, const float* c2, const float* x_next, float* feat,
+                               float* target, float* c_out, void* stream);
+
+/* The temporal network's first increments u = x^(1) - x_n (device SoA FP32) for n_cells
+   cells of h with its installed network (u_y + c1 without one).  Used to check the
+   network against a reference.  Errors: INVALID_ARG, CUDA. */
+int npfem_ws_guess_temporal(npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
+                            const float* f_prev, const float* c1, const float* c2, float* u_out, void* stream);
+
 /* First iterate of the step (positions, device SoA FP32) for n_cells cells of h
    with the handle's current warm start: y, or y + R MLP(features).  Used to check
    the warm start against a reference.  Errors: INVALID_ARG, CUDA. */

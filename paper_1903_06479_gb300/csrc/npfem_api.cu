@@ -106,6 +106,7 @@ int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv, const void* min
     if ((rc = upload(h, H.ring_ct, &tp->ring_ct))) return rc;
     if ((rc = upload(h, H.rest_c, &tp->rest_c))) return rc;
     tp->mlp = nullptr;
+    tp->tmlp = nullptr;
     if ((rc = upload(h, H.inc_ptr, &tp->inc_ptr))) return rc;
     std::vector<unsigned> incu(H.inc_idx.begin(), H.inc_idx.end());
     if ((rc = upload(h, incu, &tp->inc_idx))) return rc;
@@ -241,7 +242,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
               T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream,
               const T* u0 = nullptr, const long long* state_offs = nullptr, const long long* stats_offs = nullptr,
               int threads = 0, const T* hist_in = nullptr, T* hist_out = nullptr, long long pos_stride = 0,
-              unsigned int* defer = nullptr)
+              unsigned int* defer = nullptr, int hist_ext = 0)
 {
     npfem_handle* h0 = meshes[0];
     LaunchArgs<T> a;
@@ -301,6 +302,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     a.hist_in = hist_in;
     a.hist_out = hist_out;
     a.pos_stride = sizeof(T) == 4 && hist_out ? pos_stride : 0;
+    a.hist_ext = sizeof(T) == 4 && hist_out ? hist_ext : 0;
     a.defer = defer;
     if (mode == 0 && h0->col_planes) {
         a.col = reinterpret_cast<const float4*>(h0->col_planes);
@@ -338,11 +340,12 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
 // One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
 int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
                  cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out, long long pos_stride,
-                 unsigned int* only, const float* col = nullptr, double col_w = 0.0)
+                 unsigned int* only, const float* col = nullptr, double col_w = 0.0, int hist_ext = 0)
 {
     if (cells == 0) return 0;
     LaunchArgs<float> a;
     memset(&a, 0, sizeof(a));
+    a.hist_ext = hist_out ? hist_ext : 0;
     a.col = reinterpret_cast<const float4*>(col);
     a.col_w = (float)col_w;
     a.u0 = u0;
@@ -455,7 +458,7 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
 // one persistent SIMT launch per block size over the other groups.
 int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
                 const void* f_ext, cudaStream_t s, npfem_cell_stats* stats, const float* u0, const void* hist_in,
-                void* hist_out, long long pos_stride)
+                void* hist_out, long long pos_stride, int hist_ext = 0)
 {
     const int prec = meshes[0]->precision;
     std::vector<long long> soff(n_groups), coff(n_groups);
@@ -502,15 +505,16 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
                 // iterations would hold up the blocks that need a contraction)
                 NPFEM_CUDA(cudaMemcpyAsync(hg->defer + 2, hg->defer + 1, sizeof(unsigned int), cudaMemcpyDeviceToDevice, s));
                 NPFEM_CUDA(cudaMemsetAsync(hg->defer, 0, 2 * sizeof(unsigned int), s));
-                int rc = run_cells<float>(&hg, 1, &cg, xg, vg, fg, nullptr, nullptr, nullptr, sg, 0, s, nullptr,
-                                          nullptr, nullptr, 512, hin, hout, pos_stride, hg->defer);
+                int rc = run_cells<float>(&hg, 1, &cg, xg, vg, fg, nullptr, nullptr, nullptr, sg, 0, s,
+                                          u0 ? u0 + soff[g] : nullptr, nullptr, nullptr, 512, hin, hout, pos_stride,
+                                          hg->defer, hist_ext);
                 if (rc) return rc;
                 only = hg->defer;
             }
             const npfem_handle* hc = meshes[0];
             const float* colg = hc->col_planes ? hc->col_planes + 4 * (soff[g] / 3) : nullptr;
             int rc = run_cells_tc(hg, cg, xg, vg, fg, sg, s, u0 ? u0 + soff[g] : nullptr, hin, hout, pos_stride, only,
-                                  colg, hc->col_w);
+                                  colg, hc->col_w, hist_ext);
             if (rc) return rc;
             done[g] = 1;
         }
@@ -537,7 +541,7 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
         else
             rc = run_cells<float>(hs.data(), (int)hs.size(), cs.data(), (float*)x, (float*)v, (const float*)f_ext,
                                   nullptr, nullptr, nullptr, stats, 0, s, u0, so.data(), co.data(), threads,
-                                  (const float*)hist_in, (float*)hist_out, pos_stride);
+                                  (const float*)hist_in, (float*)hist_out, pos_stride, nullptr, hist_ext);
         if (rc) return rc;
     }
     return 0;
@@ -572,6 +576,39 @@ int precompute_warm_start(npfem_handle* const* meshes, int n_groups, const int32
     for (int g = 0; g < n_groups; ++g) {
         if (meshes[g]->tf.ws_mode && meshes[g]->tf.mlp && cells[g] > 0)
             NPFEM_CUDA(launch_ws_increments(meshes[g], cells[g], x + off, v + off, f + off, h0->ws_u + off, false, s));
+        off += (size_t)3 * meshes[g]->n * cells[g];
+    }
+    *u0 = h0->ws_u;
+    return 0;
+}
+
+// First increments of every group along a trajectory with a temporal network, into
+// meshes[0]'s buffer at the groups' state offsets (one launch per group).
+int precompute_temporal(npfem_handle* const* meshes, int n_groups, const int32_t* cells, const float* x,
+                        const float* v, const float* f, const float* hist, long long pos_stride, cudaStream_t s,
+                        const float** u0)
+{
+    npfem_handle* h0 = meshes[0];
+    size_t total = 0;
+    for (int g = 0; g < n_groups; ++g) total += (size_t)3 * meshes[g]->n * cells[g];
+    if (total > h0->ws_u_len) {
+        if (h0->ws_u) {
+            NPFEM_CUDA(cudaStreamSynchronize(s));
+            cudaFree(h0->ws_u);
+            h0->ws_u = nullptr;
+            h0->ws_u_len = 0;
+        }
+        NPFEM_CUDA(cudaMalloc(&h0->ws_u, total * sizeof(float)));
+        h0->ws_u_len = total;
+    }
+    size_t off = 0;
+    const float* c1 = hist;                  // c_{n-1}
+    const float* c2 = hist + 3 * pos_stride;  // c_{n-2}
+    const float* fp = hist + 4 * pos_stride;  // F_{n-1}
+    for (int g = 0; g < n_groups; ++g) {
+        if (cells[g] > 0)
+            NPFEM_CUDA(launch_ws_temporal(meshes[g], cells[g], x + off, v + off, f + off, fp + off, c1 + off, c2 + off,
+                                          nullptr, nullptr, nullptr, nullptr, h0->ws_u + off, 3LL * meshes[g]->n, s));
         off += (size_t)3 * meshes[g]->n * cells[g];
     }
     *u0 = h0->ws_u;
@@ -945,6 +982,7 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
     const void* hist_in = nullptr;
     void* hist_out = nullptr;
     long long pos_stride = 0;
+    int hist_ext = 0;
     if (h0->opts.warm_history) {
         std::vector<long long> sig;
         size_t elems = 0;
@@ -952,12 +990,15 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
             sig.push_back(reinterpret_cast<long long>(meshes[g]));
             sig.push_back(cells_per_group[g]);
             elems += (size_t)3 * meshes[g]->n * cells_per_group[g];
+            if (meshes[g]->precision != NPFEM_PREC_FP64 && meshes[g]->tf.tmlp) hist_ext = 1;
         }
+        sig.push_back(hist_ext);
         // FP64: the corrections; FP32: the corrections, then the positions' rounding
-        // residues, then the FP32 positions they belong to (compensated positions)
+        // residues, then the FP32 positions they belong to (compensated positions); with a
+        // temporal network also the previous correction and the last force
         const bool f32 = h0->precision != NPFEM_PREC_FP64;
         pos_stride = f32 ? (long long)elems : 0;
-        const size_t bytes = elems * (f32 ? 3 * 4 : 8);
+        const size_t bytes = elems * (f32 ? (hist_ext ? 5 : 3) * 4 : 8);
         if (bytes > h0->hist_bytes) {
             if (h0->hist) {
                 NPFEM_CUDA(cudaStreamSynchronize(s));
@@ -980,6 +1021,12 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
         if (int rc = precompute_warm_start(meshes, n_groups, cells_per_group, (const float*)x, (const float*)v,
                                            (const float*)f_ext, s, &u0))
             return rc;
+    } else if (hist_in && hist_ext) {
+        // along a trajectory with a temporal network: u = u_y + c_{n-1} + R MLP(features)
+        // for every group (u_y + c_{n-1} where a group has no network)
+        if (int rc = precompute_temporal(meshes, n_groups, cells_per_group, (const float*)x, (const float*)v,
+                                         (const float*)f_ext, (const float*)hist_in, pos_stride, s, &u0))
+            return rc;
     }
     const bool timed = h0->tev_used + 2 <= (int)h0->tev.size();
     unsigned rec_flags = cudaEventRecordDefault;
@@ -990,7 +1037,8 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
         if (cap == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
         NPFEM_CUDA(cudaEventRecordWithFlags(h0->tev[h0->tev_used], s, rec_flags));
     }
-    int rc = step_groups(meshes, n_groups, cells_per_group, x, v, f_ext, s, stats, u0, hist_in, hist_out, pos_stride);
+    int rc = step_groups(meshes, n_groups, cells_per_group, x, v, f_ext, s, stats, u0, hist_in, hist_out, pos_stride,
+                         hist_ext);
     if (rc) h0->hist_sig.clear();
     if (!rc && timed) {
         NPFEM_CUDA(cudaEventRecordWithFlags(h0->tev[h0->tev_used + 1], s, rec_flags));

@@ -74,6 +74,7 @@ struct TopoDev {
     int kpad, rb;                // tensor-core path: K padded (16 BF16, 32 TF32), row blocks of 128
     const T* rest_c;             // [3][n] rest positions about the rest centre of mass
     const float* mlp;            // learned warm start: packed parameters, weights rounded to BF16 (or null)
+    const float* tmlp;           // temporal network along a trajectory (same layout), or null
     int ws_mode;                 // 0 none, 1 learned first iterate, 2 learned iterate kept only if g is lower
     T C, B, Dsk, kvol;           // material
     T h, inv_h2, inertia_scale;  // time step; inertia_scale = 1 + h alpha_D
@@ -135,6 +136,9 @@ struct LaunchArgs {
     const T* u0;       // precomputed learned first increments x^(1) - x_n ([3][n] per cell) or null
     const T* hist_in;  // previous step's converged corrections x_n - y_{n-1} ([3][n] per cell) or null
     T* hist_out;       // this step's corrections x_{n+1} - y_n are written here (or null)
+    // 1: a temporal network is in use: finish() also keeps the previous correction at
+    // hist_out + 3 pos_stride and this step's force at hist_out + 4 pos_stride
+    int hist_ext;
     // > 0 (FP32 with hist_out): the rounding residue of each stored position, the part of
     // x_n + u below FP32 precision, sits at hist_out + pos_stride and the FP32 value it
     // belongs to at hist_out + 2 pos_stride; hist_in != null marks both as this trajectory's
@@ -219,6 +223,12 @@ cudaError_t launch_cells_tc(const LaunchArgs<float>& a, int cluster, int block, 
 // when positions is set) of n_cells cells of handle h (npfem_learn.cu).
 cudaError_t launch_ws_increments(const npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
                                  float* out, bool positions, cudaStream_t s);
+// Temporal network's first increments u = u_y + c_{n-1} (+ R MLP(features) when the
+// handle has a network), or, for training, features/targets/corrections; cells are
+// `stride` elements apart.
+cudaError_t launch_ws_temporal(const npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
+                               const float* f_prev, const float* c1, const float* c2, const float* x_next, float* feat,
+                               float* target, float* c_out, float* out, long long stride, cudaStream_t s);
 // Largest mesh the tensor-core path takes: A block (kpad / 2 columns) plus a
 // 32-column accumulator within 512 TMEM columns, and at most 8 blocks per cluster.
 constexpr int kTcMaxVerts = 960;
@@ -315,6 +325,7 @@ struct npfem_handle {
     int use_tc = 1;     // BF16: use the tensor-core cluster kernel when the mesh fits it
     // buffers of npfem_step_host
     float* mlp = nullptr;       // learned warm start parameters on the device (weights BF16-rounded)
+    float* tmlp = nullptr;      // temporal network parameters on the device
     void* hx = nullptr;
     void* hv = nullptr;
     void* hf = nullptr;

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -131,6 +132,145 @@ __global__ void __launch_bounds__(512, 2) ws_increment_kernel(const TopoDev<floa
             }
         }
         __syncthreads();
+    }
+}
+
+// Temporal network (an addition to the paper's method): along a trajectory, the first
+// iterate y_n + c_{n-1} + R MLP(features), c_k = x_{k+1} - y_k the converged correction
+// of step k.  Features of vertex i in the rest frame: the trend R^T (c_{n-1} - c_{n-2}),
+// the force change as a displacement w_i = R^T h^2 (F_n - F_{n-1})_i / m_i, and its
+// cotangent Laplacian over the one-ring.  One block per cell.  Inference (tp.tmlp set
+// and out given): out = u_y + c_{n-1} + R o (increments relative to x_n; without a
+// network, u_y + c_{n-1}).  Training: the feature rows into feat, and with x_next the
+// target R^T (c_n - c_{n-1}) and c_n itself (c_out).
+__global__ void __launch_bounds__(512, 2) ws_temporal_kernel(const TopoDev<float> tp, int n_cells, const float* x,
+                                                            const float* v, const float* f, const float* f_prev,
+                                                            const float* c1, const float* c2, const float* x_next,
+                                                            float* feat, float* target, float* c_out, float* out,
+                                                            long long stride)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = tp.n, np = tp.n_pad, tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
+    const int n16 = (n + 15) & ~15;
+    float* Y = reinterpret_cast<float*>(smem + kFixedSmem);
+    float* D = Y + 3 * np;
+    float* UY = D + 3 * np;
+    float* Wd = UY + 3 * np;  // world-frame h^2 (F_n - F_{n-1}) / m
+    float* Xs = Wd + 3 * np;  // [n16][16] normalised features (inference)
+    CellShared<float>* sh = cell_shared<float>(smem);
+    const float h = tp.h, inv_ms = 1.f / tp.inertia_scale;
+    const float* P = tp.tmlp;
+    for (int cell = blockIdx.x; cell < n_cells; cell += gridDim.x) {
+        const long long so = (long long)cell * stride;
+        const float o[3] = {x[so], x[so + n], x[so + 2 * n]};
+        for (int e = tid; e < 3 * np; e += NT) {
+            const int c = e / np, i = e - c * np;
+            float yv = 0.f, uy = 0.f, wd = 0.f;
+            if (i < n) {
+                const float im = __ldg(&tp.inv_mass[i]);
+                uy = (h * v[so + c * n + i] + h * h * f[so + c * n + i] * im) * inv_ms;
+                yv = (x[so + c * n + i] - o[c]) + uy;
+                wd = h * h * (f[so + c * n + i] - f_prev[so + c * n + i]) * im;
+            }
+            Y[e] = yv;
+            UY[e] = uy;
+            Wd[e] = wd;
+        }
+        __syncthreads();
+        ws_frame(tp, Y, D, smem);
+        float R[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) R[q] = sh->post[q];
+        const bool infer = out && P;
+        for (int i = tid; i < (infer ? n16 : n); i += NT) {
+            float ft[kMlpIn];
+            if (i < n) {
+                float lap[3] = {0.f, 0.f, 0.f};
+                const float wi[3] = {Wd[i], Wd[np + i], Wd[2 * np + i]};
+                if (tp.k8) {
+                    int jr[8];
+                    float cw[8];
+                    ring8_indices(tp.ring8_idx, i, jr);
+                    ldg8(tp.ring8_c + 8 * i, cw);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (jr[q] == i) continue;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) lap[c] += cw[q] * (Wd[c * np + jr[q]] - wi[c]);
+                    }
+                } else {
+                    for (int q = tp.ring_ptr[i]; q < tp.ring_ptr[i + 1]; ++q) {
+                        const int j = tp.ring_idx[q];
+                        const float cq = tp.ring_c[q];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) lap[c] += cq * (Wd[c * np + j] - wi[c]);
+                    }
+                }
+                float tr[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tr[c] = c1[so + c * n + i] - c2[so + c * n + i];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    ft[b] = R[b] * tr[0] + R[3 + b] * tr[1] + R[6 + b] * tr[2];
+                    ft[3 + b] = R[b] * wi[0] + R[3 + b] * wi[1] + R[6 + b] * wi[2];
+                    ft[6 + b] = R[b] * lap[0] + R[3 + b] * lap[1] + R[6 + b] * lap[2];
+                }
+            }
+            if (infer) {
+                float4* row = reinterpret_cast<float4*>(Xs + 16 * i);
+                float xv[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    xv[k] = (k < kMlpIn && i < n) ? (ft[k] - P[kPMu + k]) / P[kPSig + k] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) row[q] = make_float4(xv[4 * q], xv[4 * q + 1], xv[4 * q + 2], xv[4 * q + 3]);
+                continue;
+            }
+            if (feat) {
+                float* fo = feat + ((long long)cell * n + i) * kMlpIn;
+#pragma unroll
+                for (int k = 0; k < kMlpIn; ++k) fo[k] = ft[k];
+            }
+            if (x_next) {
+                float cn[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cn[c] = (x_next[so + c * n + i] - x[so + c * n + i]) - UY[c * np + i];
+                if (c_out)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) c_out[so + c * n + i] = cn[c];
+                if (target) {
+                    float dl[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) dl[c] = cn[c] - c1[so + c * n + i];
+                    float* t = target + ((long long)cell * n + i) * kMlpOut;
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) t[b] = R[b] * dl[0] + R[3 + b] * dl[1] + R[6 + b] * dl[2];
+                }
+            }
+            if (out && !P)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[so + c * n + i] = UY[c * np + i] + c1[so + c * n + i];
+        }
+        __syncthreads();
+        if (infer) {
+            for (int tile = tid >> 5; tile * 16 < n; tile += NT >> 5) {
+                float olo[3], ohi[3];
+                mlp_warp16(P, Xs + 256 * tile, olo, ohi);
+                if ((lane & 3) == 0) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int i = tile * 16 + (lane >> 2) + 8 * r;
+                        if (i >= n) continue;
+                        const float* oo = r ? ohi : olo;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            out[so + c * n + i] = UY[c * np + i] + c1[so + c * n + i] +
+                                                  (R[3 * c] * oo[0] + R[3 * c + 1] * oo[1] + R[3 * c + 2] * oo[2]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -317,6 +457,23 @@ constexpr size_t kGradSmem = sizeof(float) * (kMlpParams + kMlpTrainable + 4 + k
 
 }  // namespace
 
+cudaError_t launch_ws_temporal(const npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
+                               const float* f_prev, const float* c1, const float* c2, const float* x_next, float* feat,
+                               float* target, float* c_out, float* out, long long stride, cudaStream_t s)
+{
+    if (n_cells <= 0) return cudaSuccess;
+    const int np = h->n_pad, n16 = (h->n + 15) & ~15;
+    const int smem = kFixedSmem + 12 * np * (int)sizeof(float) + 16 * n16 * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(ws_temporal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int per_sm = smem <= h->smem_optin / 2 ? 2 : 1;
+    const int grid = std::min(n_cells, per_sm * h->sm_count);
+    ws_temporal_kernel<<<grid, 512, smem, s>>>(h->tf, n_cells, x, v, f, f_prev, c1, c2, x_next, feat, target, c_out,
+                                               out, stride);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ws_increments(const npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
                                  float* out, bool positions, cudaStream_t s)
 {
@@ -402,6 +559,89 @@ int npfem_ws_features(npfem_handle* h, int n_cells, const float* x, const float*
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_ws_features: ") + cudaGetErrorString(e));
     return 0;
+}
+
+int npfem_ws_features_temporal(npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
+                               const float* f_prev, const float* c1, const float* c2, const float* x_next, float* feat,
+                               float* target, float* c_out, void* stream)
+{
+    if (!h || n_cells < 0 || !x || !v || !f || !f_prev || !c1 || !c2 || (target && !x_next) || (c_out && !x_next))
+        return set_error(NPFEM_ERR_INVALID_ARG, "npfem_ws_features_temporal: bad argument");
+    if (h->precision == NPFEM_PREC_FP64)
+        return set_error(NPFEM_ERR_INVALID_ARG, "npfem_ws_features_temporal: FP32 state handles only");
+    TopoDev<float> tp = h->tf;
+    tp.tmlp = nullptr;  // features only
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_cells == 0) return 0;
+    const int np = h->n_pad, n16 = (h->n + 15) & ~15;
+    const int smem = kFixedSmem + 12 * np * (int)sizeof(float) + 16 * n16 * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(ws_temporal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) {
+        const int grid = std::min(n_cells, 2 * h->sm_count);
+        ws_temporal_kernel<<<grid, 512, smem, s>>>(tp, n_cells, x, v, f, f_prev, c1, c2, x_next, feat, target, c_out,
+                                                   nullptr, 3LL * h->n);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_ws_features_temporal: ") + cudaGetErrorString(e));
+    return 0;
+}
+
+int npfem_ws_guess_temporal(npfem_handle* h, int n_cells, const float* x, const float* v, const float* f,
+                            const float* f_prev, const float* c1, const float* c2, float* u_out, void* stream)
+{
+    if (!h || n_cells < 0 || !x || !v || !f || !f_prev || !c1 || !c2 || !u_out)
+        return set_error(NPFEM_ERR_INVALID_ARG, "npfem_ws_guess_temporal: bad argument");
+    if (h->precision == NPFEM_PREC_FP64)
+        return set_error(NPFEM_ERR_INVALID_ARG, "npfem_ws_guess_temporal: FP32 state handles only");
+    cudaError_t e = launch_ws_temporal(h, n_cells, x, v, f, f_prev, c1, c2, nullptr, nullptr, nullptr, nullptr, u_out,
+                                       3LL * h->n, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_error(NPFEM_ERR_CUDA, std::string("npfem_ws_guess_temporal: ") + cudaGetErrorString(e));
+    return 0;
+}
+
+int npfem_set_warmstart_temporal(npfem_handle* h, const float* params_host)
+{
+    if (!h) return set_error(NPFEM_ERR_INVALID_ARG, "npfem_set_warmstart_temporal: null handle");
+    if (h->precision == NPFEM_PREC_FP64)
+        return set_error(NPFEM_ERR_INVALID_ARG, "npfem_set_warmstart_temporal: FP32 state handles only");
+    if (params_host && h->mat.beta_D != 0.0)
+        return set_error(NPFEM_ERR_INVALID_ARG,
+                         "npfem_set_warmstart_temporal: the network's features use the lumped first guess; beta_D > 0 "
+                         "is not supported");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) cudaSetDevice(h->device);
+    int rc = 0;
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (!params_host) {
+        h->tf.tmlp = nullptr;
+    } else {
+        if (!h->tmlp) {
+            int err = 0;
+            h->tmlp = h->alloc<float>(kMlpDeviceWords, &err);
+            if (!h->tmlp) rc = err;
+        }
+        if (!rc) {
+            std::vector<float> r(kMlpDeviceWords, 0.f);
+            for (int q = 0; q < kMlpParams; ++q) {
+                const bool weight = (q < kPB1) || (q >= kPW2 && q < kPB2) || (q >= kPW3 && q < kPB3);
+                r[q] = weight ? bf16_round(params_host[q]) : params_host[q];
+            }
+            for (int w = 0; w < kMlpDeviceWords - kFragW1; ++w) {
+                const uint32_t word = mlp_fragment_word(params_host, w);
+                memcpy(&r[kFragW1 + w], &word, 4);
+            }
+            cudaError_t e = cudaMemcpy(h->tmlp, r.data(), sizeof(float) * kMlpDeviceWords, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess)
+                rc = set_error(NPFEM_ERR_CUDA, std::string("npfem_set_warmstart_temporal: ") + cudaGetErrorString(e));
+            else
+                h->tf.tmlp = h->tmlp;
+        }
+    }
+    h->hist_sig.clear();  // the trajectory state's layout changes with the network
+    if (dev != h->device) cudaSetDevice(dev);
+    return rc;
 }
 
 int npfem_set_warmstart(npfem_handle* h, const float* params_host, int mode)

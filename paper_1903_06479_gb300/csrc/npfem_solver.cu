@@ -953,7 +953,15 @@ struct CellSolver {
         // learned warm start: u = u_y + R MLP(features at y)
         // temporal warm start: u = u_y + (x_n - y_{n-1}) of this cell's previous step
         const int ws = (!eval_mode && !hist && T_.mlp) ? T_.ws_mode : 0;
-        if (hist) {
+        if (hist && a->hist_ext && a->u0) {
+            // temporal network: u = u_y + c_{n-1} + R MLP(features), computed before the launch
+            const T* U0 = a->u0 + so;
+            for (int e = tid; e < N3; e += NT) {
+                const int c = e / np, i = e - c * np;
+                u[e] = i < n ? U0[c * n + i] : T(0);
+            }
+            __syncthreads();
+        } else if (hist) {
             const T* Hc = a->hist_in + so;
             for (int e = tid; e < N3; e += NT) {
                 const int c = e / np, i = e - c * np;
@@ -1456,10 +1464,18 @@ struct CellSolver {
             }
         }
         if (a->hist_out) {
-            // the converged correction x_{n+1} - y_n for the next step's first iterate
+            // the converged correction x_{n+1} - y_n for the next step's first iterate; with a
+            // temporal network the one it replaces and this step's force are kept too
             T* Hc = a->hist_out + so;
+            T* Cp = a->hist_ext ? a->hist_out + 3 * a->pos_stride + so : nullptr;
+            T* Fp = a->hist_ext ? a->hist_out + 4 * a->pos_stride + so : nullptr;
+            const T* fc = a->f + so;
             for (int e = tid; e < 3 * n; e += NT) {
                 const int c = e / n, i = e - c * n;
+                if (Cp) {
+                    Cp[e] = a->hist_in ? Hc[e] : T(0);
+                    Fp[e] = fc[e];
+                }
                 Hc[e] = nonfinite ? T(0) : u[c * np + i] - UYv[c * np + i];
             }
         }

@@ -118,3 +118,58 @@ def train_warmstart(handle: N.Handle, n_cells: int = 1000, steps: int = 200, see
     P, hist = train(P, feat, target, steps=train_steps, seed=seed, log_every=log_every)
     return P, {"samples": int(feat.shape[0]), "step_pairs": n_cells * steps, "loss_init": base,
                "loss_final": validation_loss(P, feat, target), "history": hist}
+
+
+def generate_temporal(handle: N.Handle, n_cells: int, steps: int, seed: int, vertices_per_step: int = 32,
+                      tol: float = 1e-7, noise_pN: float = 0.5, regen_fraction: float = 0.5,
+                      gamma_range=(10.0, 1000.0)):
+    """Training data of the temporal network: trajectories of the plain solver from rest,
+    the first cells under a force held fixed, the last `regen_fraction` of them with the
+    N(0, noise_pN) noise redrawn every step; (features, targets) of steps >= 2 at
+    `vertices_per_step` random vertices per cell and step (device tensors)."""
+    import torch
+    pop = W.population(handle.n, n_cells, seed, forces="shear", noise_pN=noise_pN, gamma_range=gamma_range)
+    mk = lambda a: torch.tensor(W.to_soa(a), dtype=torch.float32, device="cuda")
+    x, v, f, fsh = mk(pop["x"]), mk(pop["v"]), mk(pop["f"]), mk(pop["f_shear"])
+    n = handle.n
+    plain = N.Handle(pop["rest"], pop["tris"], handle.material,
+                     N.default_opts(precision="fp32", tol=tol, max_iter=200, warm_history=0), dt=handle.dt)
+    regen = int(round(regen_fraction * n_cells))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    c1, c2 = torch.zeros_like(x), torch.zeros_like(x)
+    cn = torch.zeros_like(x)
+    f_prev = f.clone()
+    feat_all = torch.empty((n_cells * n, 9), dtype=torch.float32, device="cuda")
+    tgt_all = torch.empty((n_cells * n, 3), dtype=torch.float32, device="cuda")
+    feats, tgts = [], []
+    for k in range(steps):
+        if regen:
+            f[n_cells - regen:] = fsh[n_cells - regen:] + noise_pN * torch.randn(
+                fsh[n_cells - regen:].shape, device="cuda", generator=g)
+        x0, v0 = x.clone(), v.clone()
+        N.step([plain], [n_cells], x, v, f, plain.dt)
+        plain.ws_features_temporal(n_cells, x0, v0, f, f_prev, c1, c2, feat_all, x_next=x, target=tgt_all, c_out=cn)
+        if k >= 2:
+            pick = torch.randint(0, n, (n_cells, vertices_per_step), device="cuda", generator=g)
+            rows = (torch.arange(n_cells, device="cuda")[:, None] * n + pick).reshape(-1)
+            feats.append(feat_all[rows].clone())
+            tgts.append(tgt_all[rows].clone())
+        c2, c1 = c1, cn.clone()
+        f_prev = f.clone()
+    torch.cuda.synchronize()
+    plain.close()
+    return torch.cat(feats), torch.cat(tgts)
+
+
+def train_temporal_warmstart(handle: N.Handle, n_cells: int = 500, steps: int = 60, seed: int = 300,
+                             train_steps: int = 20000, vertices_per_step: int = 32, regen_fraction: float = 0.5):
+    """Full pipeline of the temporal network: generate, normalise, train.  Returns
+    (params, info)."""
+    feat, target = generate_temporal(handle, n_cells, steps, seed, vertices_per_step=vertices_per_step,
+                                     regen_fraction=regen_fraction)
+    P = set_normalisation(init_params(seed), feat, target)
+    base = validation_loss(P, feat, target)
+    P, hist = train(P, feat, target, steps=train_steps, seed=seed)
+    return P, {"samples": int(feat.shape[0]), "step_pairs": n_cells * (steps - 2), "loss_init": base,
+               "loss_final": validation_loss(P, feat, target), "history": hist}

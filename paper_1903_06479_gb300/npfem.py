@@ -64,7 +64,8 @@ EXPORTS = ("npfem_default_opts", "npfem_create", "npfem_destroy", "npfem_step", 
            "npfem_kernel_timing", "npfem_kernel_times", "npfem_graph_create", "npfem_graph_launch",
            "npfem_graph_destroy", "npfem_kernel_time_last", "npfem_autotune", "npfem_get_tuning",
            "npfem_flag_wait_timeout", "npfem_ibm_forces", "npfem_ibm_interpolate", "npfem_ibm_forcing",
-           "npfem_collision_detect", "npfem_set_collisions")
+           "npfem_collision_detect", "npfem_set_collisions", "npfem_set_warmstart_temporal",
+           "npfem_ws_features_temporal", "npfem_ws_guess_temporal")
 
 
 def lib_path() -> str:
@@ -100,6 +101,9 @@ def lib():
         L.npfem_get_rest_info.argtypes = [vp, vp, vp]
         L.npfem_check_device.argtypes = [vp]
         L.npfem_flag_wait_timeout.argtypes = [vp]
+        L.npfem_set_warmstart_temporal.argtypes = [vp, vp]
+        L.npfem_ws_features_temporal.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.npfem_ws_guess_temporal.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.npfem_collision_detect.argtypes = [vp, i32, vp, vp, C.c_double, vp, vp, vp]
         L.npfem_set_collisions.argtypes = [vp, vp, C.c_double]
         L.npfem_ibm_forces.argtypes = [vp, i32, vp, vp, C.POINTER(Lattice), vp, C.c_double, i32, vp, vp]
@@ -201,6 +205,25 @@ class Handle:
     def ws_features(self, n_cells, x, v, f, feat, x_next=None, target=None, stream=None):
         _check(lib().npfem_ws_features(self._h, n_cells, _addr(x), _addr(v), _addr(f), _addr(x_next), _addr(feat),
                                        _addr(target), _addr(stream)))
+
+    def set_warmstart_temporal(self, params: np.ndarray | None):
+        """Installs (5016 FP32 parameters) or removes the temporal network."""
+        if params is None:
+            _check(lib().npfem_set_warmstart_temporal(self._h, None))
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            assert p.size == mlp_nparam()
+            _check(lib().npfem_set_warmstart_temporal(self._h, p.ctypes.data))
+
+    def ws_features_temporal(self, n_cells, x, v, f, f_prev, c1, c2, feat, x_next=None, target=None, c_out=None,
+                             stream=None):
+        _check(lib().npfem_ws_features_temporal(self._h, n_cells, _addr(x), _addr(v), _addr(f), _addr(f_prev),
+                                                _addr(c1), _addr(c2), _addr(x_next), _addr(feat), _addr(target),
+                                                _addr(c_out), _addr(stream)))
+
+    def ws_guess_temporal(self, n_cells, x, v, f, f_prev, c1, c2, u_out, stream=None):
+        _check(lib().npfem_ws_guess_temporal(self._h, n_cells, _addr(x), _addr(v), _addr(f), _addr(f_prev), _addr(c1),
+                                             _addr(c2), _addr(u_out), _addr(stream)))
 
     def ws_guess(self, n_cells, x, v, f, x1, stream=None):
         _check(lib().npfem_ws_guess(self._h, n_cells, _addr(x), _addr(v), _addr(f), _addr(x1), _addr(stream)))

@@ -143,3 +143,80 @@ def test_trained_network_cuts_iterations(npfem):
         assert (s["status"] == 0).all() and (s["residual"] <= 1e-6).all()
         iters[mode] = float(s["iterations"].mean())
     assert iters[1] < iters[0] - 0.5, iters
+
+
+# ---------------------------------------------------------------------------------
+# temporal network along a trajectory
+# ---------------------------------------------------------------------------------
+def _temporal_inputs(seed, m, cells=3):
+    p = population32(642, cells, seed=seed, forces="shear", noise_pN=1.0, box=20.0)
+    rng = np.random.default_rng(seed + 1)
+    r32 = lambda a: a.astype(np.float32).astype(np.float64)
+    p["x"] = r32(p["x"] + 0.01 * m.lbar * rng.standard_normal(p["x"].shape))
+    f_prev = r32(p["f"] + rng.normal(0, 0.5, p["f"].shape))
+    c1 = r32(1e-3 * rng.standard_normal(p["x"].shape))
+    c2 = r32(c1 + 2e-4 * rng.standard_normal(p["x"].shape))
+    return p, f_prev, c1, c2
+
+
+def test_temporal_features_targets_and_corrections_match_oracle(npfem):
+    import torch
+    m, rest, tris = oracle_model(642)
+    h = npfem.Handle(rest, tris, npfem.material(), npfem.default_opts(precision="fp32"), dt=DT)
+    p, f_prev, c1, c2 = _temporal_inputs(60, m)
+    xn = (p["x"] + 1e-4 * np.random.default_rng(61).standard_normal(p["x"].shape)).astype(np.float32).astype(np.float64)
+    S = lambda a: dev(W.to_soa(a))
+    feat = torch.zeros((3 * 642, 9), device="cuda")
+    tgt = torch.zeros((3 * 642, 3), device="cuda")
+    cn = torch.zeros((3, 3, 642), device="cuda")
+    h.ws_features_temporal(3, S(p["x"]), S(p["v"]), S(p["f"]), S(f_prev), S(c1), S(c2), feat, x_next=S(xn),
+                           target=tgt, c_out=cn)
+    fg = feat.cpu().numpy().reshape(3, 642, 9)
+    tg = tgt.cpu().numpy().reshape(3, 642, 3)
+    cg = W.from_soa(cn.double().cpu().numpy())
+    for c in range(3):
+        y = m.first_guess(p["x"][c], p["v"][c], p["f"][c])
+        fo, R = m.ws_features_temporal(y, p["f"][c], f_prev[c], c1[c], c2[c])
+        scale = np.abs(fo).max(0)
+        assert np.all(np.abs(fg[c] - fo).max(0) <= 2e-4 * scale + 1e-12), (np.abs(fg[c] - fo).max(0), scale)
+        co = xn[c] - y
+        assert np.abs(cg[c] - co).max() <= 2e-4 * np.abs(co).max() + 4e-6
+        to = (co - c1[c]) @ R
+        assert np.abs(tg[c] - to).max() <= 2e-4 * np.abs(co).max() + 4e-6
+
+
+def test_temporal_guess_matches_oracle(npfem):
+    import torch
+    m, rest, tris = oracle_model(642)
+    h = npfem.Handle(rest, tris, npfem.material(), npfem.default_opts(precision="fp32"), dt=DT)
+    P = rand_params(62)
+    P[-3:] = 1e-4
+    h.set_warmstart_temporal(P.astype(np.float32))
+    p, f_prev, c1, c2 = _temporal_inputs(63, m, cells=2)
+    S = lambda a: dev(W.to_soa(a))
+    u = torch.zeros((2, 3, 642), device="cuda")
+    h.ws_guess_temporal(2, S(p["x"]), S(p["v"]), S(p["f"]), S(f_prev), S(c1), S(c2), u)
+    ug = W.from_soa(u.double().cpu().numpy())
+    for c in range(2):
+        xo = m.ws_guess_temporal(P.astype(np.float32).astype(np.float64), p["x"][c], p["v"][c], p["f"][c], f_prev[c],
+                                 c1[c], c2[c], True)
+        y = m.first_guess(p["x"][c], p["v"][c], p["f"][c])
+        corr = np.abs(xo - y - c1[c]).max()
+        assert corr > 1e-6
+        assert np.abs((p["x"][c] + ug[c]) - xo).max() <= 1e-3 * corr + 2 * np.spacing(np.float32(25.0))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_temporal_network_trajectory_matches_oracle(npfem, prec):
+    # any first iterate converges to the same step: 6 steps with the network installed
+    # against the oracle's 6 steps from y
+    m, rest, tris = oracle_model(642)
+    h = npfem.Handle(rest, tris, npfem.material(), npfem.default_opts(precision=prec, tol=1e-6), dt=DT)
+    P = rand_params(64)
+    P[-3:] = 1e-5
+    h.set_warmstart_temporal(P.astype(np.float32))
+    p = population32(642, 5, seed=65, forces="shear", noise_pN=0.5, box=10.0)
+    xo, vo, _ = oracle_steps(m, p["x"], p["v"], p["f"], steps=6, tol=1e-10, max_iter=200)
+    xg, vg, sg = gpu_step_device(h, p["x"], p["v"], p["f"], steps=6)
+    assert (sg["status"] == 0).all() and (sg["residual"] <= 1e-6).all()
+    assert max_rel_disp(xg, xo, m.lbar) <= 6 * 1e-5 + fp32_store_allowance(p["x"], m.lbar)
