@@ -21,8 +21,10 @@ Legs:
   legs      the same comparison (chosen vs plain, equal final residual) on the other
             workloads of the scope: the force noise redrawn every step ("regen"), the
             chosen form with one refinement sweep of the tensor-core contraction
-            ("refine1"), 16384 cells under N(0, 2 pN) + 1000/s shear ("c4"), and 4096
-            cells of mixed resolution, 40 % 258, 40 % 642, 20 % 2562 vertices ("c3")
+            ("refine1"), 16384 cells under N(0, 2 pN) + 1000/s shear ("c4"; with the
+            contraction in TF32 or BF16 and one refinement sweep: "c4_tf32",
+            "c4_bf16_refine1"), and 4096 cells of mixed resolution, 40 % 258, 40 % 642,
+            20 % 2562 vertices ("c3")
   cpu_baseline / --impl reference
             the FP64 CPU oracle on this machine's cores, on a bounded sample
 
@@ -80,7 +82,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--legs", default="all", help="extra workload legs: all, none, or a comma list of regen, "
-                    "refine1, c4, c3")
+                    "refine1, c4, c4_tf32, c4_bf16_refine1, c3")
     ap.add_argument("--force-noise-regen", type=int, default=0,
                     help="1: the N(0, 0.5 pN) force noise is redrawn every step (4 draws used in turn, copied in "
                          "outside the step's events); 0: the force is fixed over the run")
@@ -444,10 +446,11 @@ def roofline(pk, pk_kind, groups_n, leg, m, history, cells_by_group, kernel_name
 
 
 def compare_leg(N, W, torch, name, pops, counts, args, flush, ws_params, local, pk, pk_kind, fpools=None,
-                refine=0, plain=True, mat=None, ibm=False):
+                refine=0, plain=True, mat=None, ibm=False, precision=None):
     """Chosen form and plain FP32 path on the same cells, steps and residual tolerance."""
     mat = mat or {}
-    hs, shapes = make_chosen(N, W, pops, counts, args.precision, args.history, refine, ws_params, local, torch, **mat)
+    prec = precision or args.precision
+    hs, shapes = make_chosen(N, W, pops, counts, prec, args.history, refine, ws_params, local, torch, **mat)
     ffn, lat_info = ibm_force_fn(N, W, torch, hs, counts) if ibm else (None, None)
     ch = device_leg(N, W, hs, pops, counts, args.steps, args.warmup, torch, flush, kernel_times=True,
                     graph=bool(args.graph), fpools=fpools, force_fn=ffn)
@@ -559,7 +562,8 @@ def main():
     # the other workloads of the scope, each chosen vs plain at equal residual
     legs = {}
     want = set() if args.legs == "none" else (
-        {"regen", "refine1", "c4", "c3"} if args.legs == "all" else set(args.legs.split(",")))
+        {"regen", "refine1", "c4", "c4_tf32", "c4_bf16_refine1", "c3"} if args.legs == "all"
+        else set(args.legs.split(",")))
     if world > 1:
         want = set()  # the extra legs are single-GPU comparisons
     if "regen" in want and not args.force_noise_regen:
@@ -573,10 +577,24 @@ def main():
         legs["refine1"] = compare_leg(N, W, torch, "refine1", [pop], [cells], args, flush, P, local, pk, pk_kind,
                                       refine=1, plain=False)
         legs["refine1"]["form"] = "chosen form with one refinement sweep of the tensor-core contraction"
-    if "c4" in want:
+    if want & {"c4", "c4_tf32", "c4_bf16_refine1"}:
         p4 = W.population(N_VERTS, 16384, seed=3 + rank, forces="shear", gamma_fixed=1000.0, noise_pN=2.0)
-        legs["c4"] = compare_leg(N, W, torch, "c4", [p4], [16384], args, flush, P, local, pk, pk_kind)
-        legs["c4"]["workload"] = "16384 RBCs x 642-vertex discocyte, N(0,2 pN) + shear 1000/s (fixed), dt 0.1 us, tol 1e-6"
+        w4 = "16384 RBCs x 642-vertex discocyte, N(0,2 pN) + shear 1000/s (fixed), dt 0.1 us, tol 1e-6"
+        if "c4" in want:
+            legs["c4"] = compare_leg(N, W, torch, "c4", [p4], [16384], args, flush, P, local, pk, pk_kind)
+            legs["c4"]["workload"] = w4
+        # the precision configuration: the A^-1 contraction in BF16 and in TF32 on the tensor
+        # cores, each with one refinement sweep
+        if "c4_tf32" in want:
+            legs["c4_tf32"] = compare_leg(N, W, torch, "c4_tf32", [p4], [16384], args, flush, P, local, pk, pk_kind,
+                                          refine=1, plain=False, precision="tf32")
+            legs["c4_tf32"]["form"] = "TF32 tensor-core A^-1 contraction (streamed, per SIMT block) + one refinement sweep"
+            legs["c4_tf32"]["workload"] = w4
+        if "c4_bf16_refine1" in want:
+            legs["c4_bf16_refine1"] = compare_leg(N, W, torch, "c4_bf16_refine1", [p4], [16384], args, flush, P,
+                                                  local, pk, pk_kind, refine=1, plain=False, precision="bf16")
+            legs["c4_bf16_refine1"]["form"] = "BF16 tensor-core A^-1 contraction (clusters) + one refinement sweep"
+            legs["c4_bf16_refine1"]["workload"] = w4
         del p4
     if "c3" in want:
         n_all = 4096
