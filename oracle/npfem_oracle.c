@@ -733,16 +733,33 @@ static double dot3n(const double *a, const double *b, int n)
     return s;
 }
 
+static int solve_core(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st,
+                      const double *col, double wcol, double *S_io, double *Y_io, int *count_io);
+
 static int solve_col(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st, const double *col,
-                     double wcol);
+                     double wcol)
+{
+    return solve_core(m, x, y, o, st, col, wcol, NULL, NULL, NULL);
+}
 
 int or_solve(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st)
 {
     return solve_col(m, x, y, o, st, NULL, 0.0);
 }
 
-static int solve_col(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st, const double *col,
-                     double wcol)
+/* The same solve starting from *count_io history pairs carried over from an earlier  */
+/* solve (an addition to the paper's Algorithm 1, which starts every time step with   */
+/* an empty history): S_io, Y_io hold lbfgs_m vectors of 3n (AoS) each, the oldest    */
+/* pair first; on return they hold the solve's final pairs in the same order and      */
+/* *count_io their number (0 after a failed line search or a non-finite state).       */
+int or_solve_carry(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st, double *S_io,
+                   double *Y_io, int *count_io)
+{
+    return solve_core(m, x, y, o, st, NULL, 0.0, S_io, Y_io, count_io);
+}
+
+static int solve_core(const or_model *m, double *x, const double *y, const or_opts *o, or_stats *st,
+                      const double *col, double wcol, double *S_io, double *Y_io, int *count_io)
 {
     int n = m->n, N = 3 * n, M = o->lbfgs_m;
     size_t vb = sizeof(double) * N;
@@ -750,6 +767,14 @@ static int solve_col(const or_model *m, double *x, const double *y, const or_opt
     double *S = (double *)malloc(vb * (M > 0 ? M : 1)), *Y = (double *)malloc(vb * (M > 0 ? M : 1));
     double *rho = (double *)malloc(sizeof(double) * (M > 0 ? M : 1)), *al = (double *)malloc(sizeof(double) * (M > 0 ? M : 1));
     int head = 0, count = 0, bad = 0;
+    if (count_io && *count_io > 0 && M > 0) {
+        /* carried pairs into slots 0..count-1, the newest last */
+        count = *count_io < M ? *count_io : M;
+        memcpy(S, S_io, vb * count);
+        memcpy(Y, Y_io, vb * count);
+        for (int i = 0; i < count; ++i) rho[i] = 1.0 / dot3n(S + (size_t)i * N, Y + (size_t)i * N, n);
+        head = count % M;
+    }
     st->iterations = 0; st->evaluations = 1; st->status = OR_OK;
     double parts[6];
     double E = objective_col(m, x, y, g, parts, &bad, col, wcol);
@@ -819,6 +844,16 @@ static int solve_col(const or_model *m, double *x, const double *y, const or_opt
     st->objective = E;
     st->volume = or_volume(m, x);
     st->area = or_area(m, x);
+    if (count_io) {
+        /* the pairs, oldest first; none after a failure */
+        if (st->status == OR_NONFINITE || st->status == OR_LINESEARCH_FAIL) count = 0;
+        for (int q = 0; q < count; ++q) {
+            int i = (head - count + q + M) % M;
+            memcpy(S_io + (size_t)q * N, S + (size_t)i * N, vb);
+            memcpy(Y_io + (size_t)q * N, Y + (size_t)i * N, vb);
+        }
+        *count_io = count;
+    }
     free(g); free(d); free(xt); free(gt); free(S); free(Y); free(rho); free(al);
     return st->status;
 }

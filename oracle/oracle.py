@@ -84,6 +84,8 @@ def lib():
         L.or_residual.argtypes = [P, dp]
         L.or_solve.restype = C.c_int
         L.or_solve.argtypes = [P, dp, dp, C.POINTER(Opts), C.POINTER(Stats)]
+        L.or_solve_carry.restype = C.c_int
+        L.or_solve_carry.argtypes = [P, dp, dp, C.POINTER(Opts), C.POINTER(Stats), dp, dp, C.POINTER(C.c_int)]
         L.or_post_step.argtypes = [P, dp, dp, C.c_double]
         L.or_step.restype = C.c_int
         L.or_step.argtypes = [P, dp, dp, dp, C.POINTER(Opts), C.POINTER(Stats)]
@@ -273,6 +275,51 @@ class Model:
         st = Stats()
         lib().or_solve(self._h, x, np.ascontiguousarray(y, dtype=np.float64), C.byref(opts or make_opts()), C.byref(st))
         return x, st
+
+    def solve_carry(self, x0, y, pairs=None, opts: Opts | None = None):
+        """solve() starting from L-BFGS pairs carried over from an earlier solve.
+
+        pairs: (S, Y) arrays [k, n, 3], the oldest pair first (None or k = 0: an empty
+        history).  Returns (x, stats, (S, Y)) with the solve's final pairs, oldest first."""
+        o = opts or make_opts()
+        M = max(o.lbfgs_m, 1)
+        S = np.zeros((M, self.n, 3)); Y = np.zeros((M, self.n, 3))
+        k = 0
+        if pairs is not None and len(pairs[0]) > 0:
+            k = min(len(pairs[0]), o.lbfgs_m)
+            S[:k] = pairs[0][-k:]; Y[:k] = pairs[1][-k:]
+        cnt = C.c_int(k)
+        x = np.array(x0, dtype=np.float64, order="C")
+        st = Stats()
+        lib().or_solve_carry(self._h, x, np.ascontiguousarray(y, dtype=np.float64), C.byref(o), C.byref(st),
+                             S.reshape(-1), Y.reshape(-1), C.byref(cnt))
+        return x, st, (S[:cnt.value].copy(), Y[:cnt.value].copy())
+
+    def trajectory(self, x, v, f, steps, opts: Opts | None = None, carry_pairs=True):
+        """steps time steps of one cell along a trajectory with the temporal warm start:
+        step 1 starts from y, each later step from y_n + (x_n - y_{n-1}), the previous
+        step's converged correction (an addition to the paper's Algorithm 1, which starts
+        from y); with carry_pairs each solve also starts from the previous solve's L-BFGS
+        pairs.  f: one force [n, 3] or a sequence of steps forces.  Returns (x, v, stats
+        of every step)."""
+        x = np.array(x, dtype=np.float64); v = np.array(v, dtype=np.float64)
+        kappa = float(self.material[MATERIAL_ORDER.index("kappa")])
+        corr, pairs, out = None, None, []
+        for k in range(steps):
+            fk = np.asarray(f[k] if np.ndim(f) == 3 else f, dtype=np.float64)
+            y = self.first_guess(x, v, fk)
+            x0 = y if corr is None else y + corr
+            x1, st, p = self.solve_carry(x0, y, pairs if carry_pairs else None, opts)
+            pairs = p
+            if st.status == 3:  # non-finite: the cell keeps x_n, no correction is kept
+                x1 = x.copy()
+                corr = np.zeros_like(x)
+            else:
+                corr = x1 - y
+            v = self.post_step(x1, (x1 - x) / self.dt, kappa)
+            x = x1
+            out.append(st)
+        return x, v, out
 
     def post_step(self, x, v, kappa):
         v = np.array(v, dtype=np.float64, order="C")
