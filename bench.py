@@ -73,7 +73,9 @@ def parse():
     ap.add_argument("--cells", type=int, default=1024)
     ap.add_argument("--precision", default="bf16")
     ap.add_argument("--warmstart", default="learned", choices=["learned", "none"])
-    ap.add_argument("--history", type=int, default=1, help="1: temporal warm start from the previous step")
+    ap.add_argument("--history", type=int, default=2,
+                    help="1: temporal warm start from the previous step; 2: also the previous solve's L-BFGS pairs "
+                         "while it took at most 3 iterations")
     ap.add_argument("--ws-train-steps", type=int, default=100000)
     ap.add_argument("--ws-vertices", type=int, default=32, help="training vertices sampled per cell and step")
     ap.add_argument("--graph", type=int, default=1, help="1: each timed step replays a captured CUDA graph")
@@ -197,11 +199,12 @@ def algorithmic_bytes(n, m, iters, evals, cells):
     return cells * 5 * vb + iters * (4 * m + 6) * vb + evals * 2 * vb
 
 
-def trajectory_bytes(n, cells):
+def trajectory_bytes(n, cells, history=1, m=5):
     """Bytes of the library's trajectory state per step (not algorithmic): the last
     correction and the positions' rounding residues with their FP32 values, each read
-    and written, 6*12n per cell."""
-    return cells * 6 * 12 * n
+    and written, 6*12n per cell; with carried L-BFGS pairs (history 2) at most one read
+    and one write of each cell's record (2m vectors of 12n bytes) on top."""
+    return cells * (6 + (4 * m if history == 2 else 0)) * 12 * n
 
 
 def peaks():
@@ -436,7 +439,7 @@ def roofline(pk, pk_kind, groups_n, leg, m, history, cells_by_group, kernel_name
     kms = leg["kernel_ms"]
     t = float(np.mean(kms)) / 1e3 if kms is not None and len(kms) else leg["ms_per_step"] / 1e3
     achieved = alg / t / 1e9
-    impl = sum(trajectory_bytes(n, c) for n, c in zip(groups_n, cells_by_group)) if history else 0
+    impl = sum(trajectory_bytes(n, c, history, m) for n, c in zip(groups_n, cells_by_group)) if history else 0
     return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_source": (f"{pk_kind} (HBM copy bandwidth, MEASURED_PEAKS.json)" if pk_kind == "measured"
@@ -630,7 +633,9 @@ def main():
                            "cells_per_gpu": cells, "precision": prec_name,
                            "forces": FORCES_REGEN if args.force_noise_regen else FORCES_FIXED,
                            "warm_start": ("learned MLP" if P is not None else "first guess y")
-                           + (" (first step), then previous step's correction" if args.history else ""),
+                           + (" (first step), then previous step's correction" if args.history else "")
+                           + (" and L-BFGS pairs (while the last solve took <= 3 iterations)"
+                              if args.history == 2 else ""),
                            "lbfgs_m": 5, "refine": 0,
                            "launch": "CUDA graph of one step per timed step" if args.graph else "npfem_step per step",
                            "launch_shape": shapes[0] if shapes is not None else "default",

@@ -295,22 +295,24 @@ class Model:
                              S.reshape(-1), Y.reshape(-1), C.byref(cnt))
         return x, st, (S[:cnt.value].copy(), Y[:cnt.value].copy())
 
-    def trajectory(self, x, v, f, steps, opts: Opts | None = None, carry_pairs=True):
+    def trajectory(self, x, v, f, steps, opts: Opts | None = None, carry_pairs=True, carry_max_iters=None):
         """steps time steps of one cell along a trajectory with the temporal warm start:
         step 1 starts from y, each later step from y_n + (x_n - y_{n-1}), the previous
         step's converged correction (an addition to the paper's Algorithm 1, which starts
         from y); with carry_pairs each solve also starts from the previous solve's L-BFGS
-        pairs.  f: one force [n, 3] or a sequence of steps forces.  Returns (x, v, stats
-        of every step)."""
+        pairs, when carry_max_iters is None always, else only while the previous solve
+        took at most carry_max_iters iterations.  f: one force [n, 3] or a sequence of
+        steps forces.  Returns (x, v, stats of every step)."""
         x = np.array(x, dtype=np.float64); v = np.array(v, dtype=np.float64)
         kappa = float(self.material[MATERIAL_ORDER.index("kappa")])
-        corr, pairs, out = None, None, []
+        corr, pairs, out, last = None, None, [], 0
         for k in range(steps):
             fk = np.asarray(f[k] if np.ndim(f) == 3 else f, dtype=np.float64)
             y = self.first_guess(x, v, fk)
             x0 = y if corr is None else y + corr
-            x1, st, p = self.solve_carry(x0, y, pairs if carry_pairs else None, opts)
-            pairs = p
+            use = carry_pairs and (carry_max_iters is None or last <= carry_max_iters)
+            x1, st, p = self.solve_carry(x0, y, pairs if use else None, opts)
+            pairs, last = p, st.iterations
             if st.status == 3:  # non-finite: the cell keeps x_n, no correction is kept
                 x1 = x.copy()
                 corr = np.zeros_like(x)

@@ -232,8 +232,8 @@ int check_opts(const npfem_opts* o)
     if (o->refine < 0 || o->refine > 1) return fail(NPFEM_ERR_INVALID_ARG, "opts.refine must be 0 or 1");
     if (o->fill_idle_sms < 0 || o->fill_idle_sms > 1)
         return fail(NPFEM_ERR_INVALID_ARG, "opts.fill_idle_sms must be 0 or 1");
-    if (o->warm_history < 0 || o->warm_history > 1)
-        return fail(NPFEM_ERR_INVALID_ARG, "opts.warm_history must be 0 or 1");
+    if (o->warm_history < 0 || o->warm_history > 2)
+        return fail(NPFEM_ERR_INVALID_ARG, "opts.warm_history must be 0, 1 or 2");
     return 0;
 }
 
@@ -242,7 +242,8 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
               T* grad_out, double* parts, npfem_cell_stats* stats, int mode, cudaStream_t stream,
               const T* u0 = nullptr, const long long* state_offs = nullptr, const long long* stats_offs = nullptr,
               int threads = 0, const T* hist_in = nullptr, T* hist_out = nullptr, long long pos_stride = 0,
-              unsigned int* defer = nullptr, int hist_ext = 0)
+              unsigned int* defer = nullptr, int hist_ext = 0, T* carry = nullptr,
+              const long long* carry_offs = nullptr)
 {
     npfem_handle* h0 = meshes[0];
     LaunchArgs<T> a;
@@ -267,6 +268,8 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
         g.state_off = state_offs ? state_offs[gi] : state;
         g.stats_off = stats_offs ? stats_offs[gi] : total;
         g.cells = cells[gi];
+        g.carry_rec = carry_rec_elems(h->n_pad, h0->opts.lbfgs_m);
+        g.carry_off = carry_offs ? carry_offs[gi] : 0;
         long long sb = 0;
         place_vectors(&g, h->n_pad, h->nt, h0->opts.lbfgs_m, budget, &sb, tcb);
         slot = std::max(slot, sb);
@@ -303,6 +306,7 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
     a.hist_out = hist_out;
     a.pos_stride = sizeof(T) == 4 && hist_out ? pos_stride : 0;
     a.hist_ext = sizeof(T) == 4 && hist_out ? hist_ext : 0;
+    a.carry = mode == 0 && hist_out ? carry : nullptr;
     a.defer = defer;
     if (mode == 0 && h0->col_planes) {
         a.col = reinterpret_cast<const float4*>(h0->col_planes);
@@ -340,12 +344,14 @@ int run_cells(npfem_handle* const* meshes, int n_groups, const int32_t* cells, T
 // One tensor-core launch for one mesh group (BF16, n <= kTcMaxVerts).
 int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f, npfem_cell_stats* stats,
                  cudaStream_t stream, const float* u0, const float* hist_in, float* hist_out, long long pos_stride,
-                 unsigned int* only, const float* col = nullptr, double col_w = 0.0, int hist_ext = 0)
+                 unsigned int* only, const float* col = nullptr, double col_w = 0.0, int hist_ext = 0,
+                 float* carry = nullptr)
 {
     if (cells == 0) return 0;
     LaunchArgs<float> a;
     memset(&a, 0, sizeof(a));
     a.hist_ext = hist_out ? hist_ext : 0;
+    a.carry = hist_out ? carry : nullptr;
     a.col = reinterpret_cast<const float4*>(col);
     a.col_w = (float)col_w;
     a.u0 = u0;
@@ -359,6 +365,8 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
     g.cell_begin = 0;
     g.state_off = 0;
     g.cells = cells;
+    g.carry_rec = carry_rec_elems(h->n_pad, h->opts.lbfgs_m);
+    g.carry_off = 0;
     const int cluster = h->tf.rb;
     const int ncol = cluster * 3 > 16 ? 32 : 16;
     const int bbytes = (ncol * h->tf.kpad * 2 + 127) & ~127;
@@ -458,16 +466,18 @@ int run_cells_tc(npfem_handle* h, int cells, float* x, float* v, const float* f,
 // one persistent SIMT launch per block size over the other groups.
 int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
                 const void* f_ext, cudaStream_t s, npfem_cell_stats* stats, const float* u0, const void* hist_in,
-                void* hist_out, long long pos_stride, int hist_ext = 0)
+                void* hist_out, long long pos_stride, int hist_ext = 0, void* carry = nullptr)
 {
     const int prec = meshes[0]->precision;
-    std::vector<long long> soff(n_groups), coff(n_groups);
-    long long st = 0, ct = 0;
+    std::vector<long long> soff(n_groups), coff(n_groups), koff(n_groups);
+    long long st = 0, ct = 0, kt = 0;
     for (int g = 0; g < n_groups; ++g) {
         soff[g] = st;
         coff[g] = ct;
+        koff[g] = kt;
         st += 3LL * meshes[g]->n * cells_per_group[g];
         ct += cells_per_group[g];
+        kt += carry_rec_elems(meshes[g]->n_pad, meshes[0]->opts.lbfgs_m) * cells_per_group[g];
     }
     std::vector<char> done(n_groups, 0);
     for (int g = 0; g < n_groups; ++g) {
@@ -484,6 +494,7 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
             npfem_cell_stats* sg = stats ? stats + coff[g] : nullptr;
             const float* hin = hist_in ? (const float*)hist_in + soff[g] : nullptr;
             float* hout = hist_out ? (float*)hist_out + soff[g] : nullptr;
+            float* kg = carry ? (float*)carry + koff[g] : nullptr;
             unsigned int* only = nullptr;
             if (hout && (size_t)cg + 3 > hg->defer_len) {
                 // allocated with the history (first call of a trajectory), so that the
@@ -507,14 +518,14 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
                 NPFEM_CUDA(cudaMemsetAsync(hg->defer, 0, 2 * sizeof(unsigned int), s));
                 int rc = run_cells<float>(&hg, 1, &cg, xg, vg, fg, nullptr, nullptr, nullptr, sg, 0, s,
                                           u0 ? u0 + soff[g] : nullptr, nullptr, nullptr, 512, hin, hout, pos_stride,
-                                          hg->defer, hist_ext);
+                                          hg->defer, hist_ext, kg);
                 if (rc) return rc;
                 only = hg->defer;
             }
             const npfem_handle* hc = meshes[0];
             const float* colg = hc->col_planes ? hc->col_planes + 4 * (soff[g] / 3) : nullptr;
             int rc = run_cells_tc(hg, cg, xg, vg, fg, sg, s, u0 ? u0 + soff[g] : nullptr, hin, hout, pos_stride, only,
-                                  colg, hc->col_w, hist_ext);
+                                  colg, hc->col_w, hist_ext, kg);
             if (rc) return rc;
             done[g] = 1;
         }
@@ -524,24 +535,27 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
         const int threads = prec == NPFEM_PREC_FP64 ? 512 : meshes[g0]->threads;
         std::vector<npfem_handle*> hs;
         std::vector<int32_t> cs;
-        std::vector<long long> so, co;
+        std::vector<long long> so, co, ko;
         for (int g = g0; g < n_groups; ++g) {
             if (done[g] || (prec != NPFEM_PREC_FP64 && meshes[g]->threads != threads)) continue;
             hs.push_back(meshes[g]);
             cs.push_back(cells_per_group[g]);
             so.push_back(soff[g]);
             co.push_back(coff[g]);
+            ko.push_back(koff[g]);
             done[g] = 1;
         }
         int rc;
         if (prec == NPFEM_PREC_FP64)
             rc = run_cells<double>(hs.data(), (int)hs.size(), cs.data(), (double*)x, (double*)v, (const double*)f_ext,
                                    nullptr, nullptr, nullptr, stats, 0, s, nullptr, so.data(), co.data(), threads,
-                                   (const double*)hist_in, (double*)hist_out);
+                                   (const double*)hist_in, (double*)hist_out, 0, nullptr, 0, (double*)carry,
+                                   ko.data());
         else
             rc = run_cells<float>(hs.data(), (int)hs.size(), cs.data(), (float*)x, (float*)v, (const float*)f_ext,
                                   nullptr, nullptr, nullptr, stats, 0, s, u0, so.data(), co.data(), threads,
-                                  (const float*)hist_in, (float*)hist_out, pos_stride, nullptr, hist_ext);
+                                  (const float*)hist_in, (float*)hist_out, pos_stride, nullptr, hist_ext,
+                                  (float*)carry, ko.data());
         if (rc) return rc;
     }
     return 0;
@@ -648,7 +662,7 @@ void npfem_default_opts(npfem_opts* o)
     o->armijo_noise = 4.0;
     o->refine = 0;
     o->fill_idle_sms = 1;
-    o->warm_history = 1;
+    o->warm_history = 2;
 }
 
 const char* npfem_last_error(void) { return g_last_error.c_str(); }
@@ -983,6 +997,7 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
     void* hist_out = nullptr;
     long long pos_stride = 0;
     int hist_ext = 0;
+    void* carry = nullptr;
     if (h0->opts.warm_history) {
         std::vector<long long> sig;
         size_t elems = 0;
@@ -1009,6 +1024,25 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
             }
             NPFEM_CUDA(cudaMalloc(&h0->hist, bytes));
             h0->hist_bytes = bytes;
+        }
+        if (h0->opts.warm_history == 2 && bytes > 0) {
+            // carried L-BFGS pairs: one record per cell, valid together with the corrections
+            size_t kb = 0;
+            for (int g = 0; g < n_groups; ++g)
+                kb += (size_t)carry_rec_elems(meshes[g]->n_pad, h0->opts.lbfgs_m) * cells_per_group[g];
+            kb *= f32 ? 4 : 8;
+            if (kb > h0->carry_bytes) {
+                if (h0->carry) {
+                    NPFEM_CUDA(cudaStreamSynchronize(s));
+                    cudaFree(h0->carry);
+                    h0->carry = nullptr;
+                    h0->carry_bytes = 0;
+                }
+                h0->hist_sig.clear();
+                NPFEM_CUDA(cudaMalloc(&h0->carry, kb));
+                h0->carry_bytes = kb;
+            }
+            carry = h0->carry;
         }
         if (bytes > 0) {
             if (sig == h0->hist_sig) hist_in = h0->hist;
@@ -1038,7 +1072,7 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
         NPFEM_CUDA(cudaEventRecordWithFlags(h0->tev[h0->tev_used], s, rec_flags));
     }
     int rc = step_groups(meshes, n_groups, cells_per_group, x, v, f_ext, s, stats, u0, hist_in, hist_out, pos_stride,
-                         hist_ext);
+                         hist_ext, carry);
     if (rc) h0->hist_sig.clear();
     if (!rc && timed) {
         NPFEM_CUDA(cudaEventRecordWithFlags(h0->tev[h0->tev_used + 1], s, rec_flags));

@@ -92,6 +92,8 @@ struct GroupDesc {
     long long stats_off;   // index of the group's first cell in stats (and eval parts)
     int cells;
     int smem_bytes;        // dynamic smem this group needs (after kFixedSmem)
+    long long carry_off;   // element offset of the group's first carried-pairs record in LaunchArgs::carry
+    long long carry_rec;   // elements per record (carry_rec_elems)
     int loc[kMaxVecs];     // >= 0: byte offset in smem; < 0: -(byte offset in the CTA's global slot) - 1
 };
 
@@ -143,6 +145,12 @@ struct LaunchArgs {
     // x_n + u below FP32 precision, sits at hist_out + pos_stride and the FP32 value it
     // belongs to at hist_out + 2 pos_stride; hist_in != null marks both as this trajectory's
     long long pos_stride;
+    // L-BFGS pairs carried across time steps (opts.warm_history = 2), one record per
+    // cell at g.carry_off + cell * g.carry_rec (layout: carry_rec_elems), or null.  With
+    // hist_in set the records hold the cell's pairs from its last solve: the first
+    // direction request of the step loads them; finish() writes them back when they
+    // changed (no write for a cell accepted at its first iterate)
+    T* carry;
     // first-iterate pass (SIMT launch): cells not accepted at x^(1) are appended to
     // defer and left untouched.  Layout: [0] cells listed, [1] listed cells that
     // needed iterations (counted by the launch that solves them), [2] that count of the
@@ -170,6 +178,21 @@ struct LaunchArgs {
     long long reserve;
     SolverParams p;
 };
+
+#ifdef __CUDACC__
+#define NPFEM_HD __host__ __device__
+#else
+#define NPFEM_HD
+#endif
+// Carried L-BFGS pairs of one cell, in elements of the state type: the solver's history
+// ring as the last solve left it: [0] the pair count, [1] the ring head, [2] that
+// solve's iterations, from [4] the inner products s_i^T y_j by ring slot (m x m, padded
+// to a multiple of 4), then the s vectors of ring slots 0..m-1 and the y vectors
+// ([3][n_pad] each).  The pairs are used while that solve took at most kCarryMaxIters
+// iterations.
+constexpr int kCarryMaxIters = 3;
+NPFEM_HD inline long long carry_head_elems(int m) { return 4 + (((long long)m * m + 3) & ~3LL); }
+NPFEM_HD inline long long carry_rec_elems(int n_pad, int m) { return carry_head_elems(m) + 2LL * m * 3 * n_pad; }
 
 // ---- host-side rest precompute (npfem_setup.cpp) ------------------------------
 struct HostTopo {
@@ -316,6 +339,9 @@ struct npfem_handle {
     void* hist = nullptr;
     size_t hist_bytes = 0;
     std::vector<long long> hist_sig;
+    // carried L-BFGS pairs (opts.warm_history = 2), one record per cell, valid with hist
+    void* carry = nullptr;
+    size_t carry_bytes = 0;
     // cells the first-iterate pass leaves to the cluster kernel ([0] count, [1] cells
     // that needed iterations, [2] the previous step's [1], then indices)
     unsigned int* defer = nullptr;
@@ -374,6 +400,9 @@ struct npfem_handle {
         hist = nullptr;
         hist_bytes = 0;
         hist_sig.clear();
+        if (carry) cudaFree(carry);
+        carry = nullptr;
+        carry_bytes = 0;
         if (defer) cudaFree(defer);
         defer = nullptr;
         defer_len = 0;

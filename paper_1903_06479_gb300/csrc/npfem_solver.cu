@@ -866,9 +866,26 @@ struct CellSolver {
     bool nonfinite;
     const float4* colp;  // this cell's collision planes, or null
     T wcol;
+    // carried L-BFGS pairs: this cell's record (or null); carry_valid: the record holds
+    // the pairs of the cell's last solve; carry_in: not yet loaded in this step
+    T* crec;
+    bool carry_valid, carry_in;
+    T ccount;  // the record's pair count, read in begin (its latency hidden by the evaluation)
+    T clast;   // the record's iteration count of the cell's last step
+    // history vectors that do not fit in shared memory live in the record (they may be
+    // carried to the next step) rather than in the block's slot
+    bool ring_in_record;
 
     __device__ const TopoDev<T>& tp() const { return gd->topo; }
-    __device__ T* hist(int v) const { return vec_ptr(*gd, smem, slot, v); }
+    // A solver vector; with carried pairs, a history vector that does not fit in shared
+    // memory lives in the cell's record (ring slot order, see load_pairs), not in the
+    // block's global slot, so that the pairs persist without a copy.
+    __device__ T* hist(int v) const
+    {
+        if (ring_in_record && v >= V_SBASE && gd->loc[v] < 0)
+            return crec + carry_head_elems(M) + (long long)(v - V_SBASE) * 3 * tp().n_pad;
+        return vec_ptr(*gd, smem, slot, v);
+    }
 
     __device__ void bind(const LaunchArgs<T>& la, const GroupDesc<T>& g_, unsigned char* sm)
     {
@@ -904,6 +921,12 @@ struct CellSolver {
         const T h = T_.h, inv_ms = T(1) / T_.inertia_scale;
         const bool eval_mode = a->p.mode == 1;
         const bool hist = !eval_mode && a->hist_in;
+        crec = (!eval_mode && a->carry) ? a->carry + gd->carry_off + cell * gd->carry_rec : nullptr;
+        carry_valid = crec && hist;
+        carry_in = carry_valid && M > 0;
+        ccount = carry_in ? crec[0] : T(0);
+        clast = carry_in ? crec[2] : T(0);
+        ring_in_record = crec && M > 0 && (!carry_in || clast <= T(kCarryMaxIters));
         const T* x = a->x + so;
         // compensated positions: x_n = x + residue while x holds exactly the value the
         // last step stored (each coordinate checked), else x alone
@@ -1088,6 +1111,118 @@ struct CellSolver {
     // History slot of the q-th newest pair.
     __device__ int hslot(int q) const { return (head - 1 - q + M) % M; }
 
+    // Pairs carried from the cell's last solve.  The record keeps the history ring as it
+    // was: [0] pair count, [1] ring head, [2] the iterations of that solve, from [4]
+    // s_i^T y_j by ring slot (m x m), then the s vectors of ring slots 0..m-1 and the y
+    // vectors.  The pairs are used while that solve took at most kCarryMaxIters
+    // iterations: under a force that changes little from step to step they cut the
+    // iterations; where each step needs several iterations anyway (a force redrawn at
+    // random every step) they save none and a full window costs more per iteration.  History vectors that live in
+    // the record are used in place (hist()); those in shared memory arrive by
+    // asynchronous 16-byte copies, all of a thread's in flight at once.  s_i^T g at the
+    // current iterate takes one block reduction.  Called at the step's first direction
+    // request, so a cell accepted at its first iterate reads nothing.
+    __device__ void load_pairs()
+    {
+        carry_in = false;
+        const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x, Mm = M;
+        if (!(ccount >= T(1)) || !(clast <= T(kCarryMaxIters))) return;
+        const int cnt = ccount < T(Mm) ? (int)ccount : Mm;
+        const T hv = crec[1];
+        const int hd = hv >= T(0) && hv < T(Mm) ? (int)hv : 0;
+        const T* V = crec + carry_head_elems(Mm);
+        for (int q = 0; q < 2 * cnt; ++q) {
+            const int i = (hd - 1 - (q >> 1) + Mm) % Mm;
+            const int r = (q & 1) ? Mm + i : i;  // s then y of each valid slot
+            if (gd->loc[V_SBASE + r] < 0) continue;  // used in place
+            const T* src = V + (long long)r * N3;
+            T* dst = hist(V_SBASE + r);
+            for (int e = 4 * tid; e < N3; e += 4 * NT) {
+#pragma unroll
+                for (int b = 0; b < (int)sizeof(T) / 4; ++b)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                     (uint32_t)__cvta_generic_to_shared(dst + e + b * (16 / sizeof(T)))),
+                                 "l"(__cvta_generic_to_global(src + e + b * (16 / sizeof(T))))
+                                 : "memory");
+            }
+        }
+        for (int k = tid; k < Mm * Mm; k += NT) sh->SY[k / Mm][k % Mm] = crec[4 + k];
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        head = hd;
+        count = cnt;
+        __syncthreads();
+        T acc[kMaxHistory];
+#pragma unroll
+        for (int q = 0; q < kMaxHistory; ++q) acc[q] = T(0);
+        for (int e = 4 * tid; e < N3; e += 4 * NT) {
+            T gv[4];
+            ld4(g + e, gv);
+#pragma unroll
+            for (int q = 0; q < kMaxHistory; ++q) {
+                if (q < cnt) {
+                    T t[4];
+                    ld4(hist(V_SBASE + hslot(q)) + e, t);
+                    acc[q] += (t[0] * gv[0] + t[1] * gv[1]) + (t[2] * gv[2] + t[3] * gv[3]);
+                }
+            }
+        }
+        block_sum<T, kMaxHistory>(acc, smem, [=](CellShared<T>* c) {
+            for (int q = 0; q < cnt; ++q) {
+                const int i = (hd - 1 - q + Mm) % Mm;
+                c->sg[i] = c->out[q];
+                c->rho[i] = T(1) / c->SY[i][i];
+            }
+        });
+    }
+
+    // This solve's pairs into the cell's record: the history vectors not already there,
+    // the inner products, the ring head, the count and the iterations.  Without an
+    // iteration the record already holds the pairs and only the iteration count (0) is
+    // written; after a failed line search, a non-finite state or more than
+    // kCarryMaxIters iterations (pairs the next step will not use) only the header.
+    __device__ void store_pairs()
+    {
+        const bool fail = nonfinite || status == NPFEM_CELL_LINESEARCH_FAIL;
+        const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x, Mm = M;
+        if (carry_valid && iters == 0 && !fail) {
+            // no iteration: the record keeps the pairs this solve would have started from
+            // (none when the rule above left them out) and records 0 iterations
+            if (tid == 0) {
+                if (!(ccount >= T(1) && clast <= T(kCarryMaxIters))) crec[0] = T(0);
+                crec[2] = T(0);
+            }
+            return;
+        }
+        if (fail || iters > kCarryMaxIters || M == 0) {
+            // pairs the next step would not use: the header alone
+            if (tid == 0) {
+                crec[0] = T(0);
+                crec[2] = T(iters);
+            }
+            return;
+        }
+        const int cnt = count;
+        T* V = crec + carry_head_elems(Mm);
+        for (int q = 0; q < 2 * cnt; ++q) {
+            const int i = hslot(q >> 1);
+            const int r = (q & 1) ? Mm + i : i;
+            if (ring_in_record && gd->loc[V_SBASE + r] < 0) continue;  // already in the record
+            const T* src = hist(V_SBASE + r);
+            T* dst = V + (long long)r * N3;
+            for (int e = 4 * tid; e < N3; e += 4 * NT) {
+                T t[4];
+                ld4(src + e, t);
+                st4(dst + e, t);
+            }
+        }
+        for (int k = tid; k < Mm * Mm; k += NT) crec[4 + k] = sh->SY[k / Mm][k % Mm];
+        if (tid == 0) {
+            crec[0] = T(cnt);
+            crec[1] = T(head);
+            crec[2] = T(iters);
+        }
+    }
+
     // First loop of the two-loop recursion (Nocedal & Wright Alg. 7.4), newest pair
     // first, on scalars: with s_i^T g and the pairs' inner products s_i^T y_j kept up to
     // date, alpha_i = rho_i (s_i^T g - sum_{j newer} alpha_j s_i^T y_j) on thread 0;
@@ -1095,6 +1230,7 @@ struct CellSolver {
     // history vectors by age for the second loop and the line search.
     __device__ void first_loop()
     {
+        if (carry_in) load_pairs();
         const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x;
         const int cnt = count;
         if (cnt > 0) {
@@ -1115,15 +1251,20 @@ struct CellSolver {
             }
             __syncthreads();
         }
+        // unrolled over the window so that a thread's loads of the pairs (some of them
+        // from global memory) are in flight together
         for (int e = 4 * tid; e < N3; e += 4 * NT) {
             T d[4];
             ld4(g + e, d);
-            for (int q = 0; q < cnt; ++q) {
-                T y[4];
-                ld4(sh->hy[q] + e, y);
-                const T al = sh->aq[q];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) d[k] -= al * y[k];
+            for (int q = 0; q < kMaxHistory; ++q) {
+                if (q < cnt) {
+                    T y[4];
+                    ld4(sh->hy[q] + e, y);
+                    const T al = sh->aq[q];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) d[k] -= al * y[k];
+                }
             }
             st4(Dv + e, d);
         }
@@ -1173,12 +1314,15 @@ struct CellSolver {
         for (int e = 4 * tid; e < N3; e += 4 * NT) {
             T r[4], gv[4];
             ld4(GCv + e, r);
-            for (int q = 0; q < cnt; ++q) {
-                T sv[4];
-                ld4(sh->hs[q] + e, sv);
-                const T cf = sh->cq[q];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) r[k] += cf * sv[k];
+            for (int q = 0; q < kMaxHistory; ++q) {
+                if (q < cnt) {
+                    T sv[4];
+                    ld4(sh->hs[q] + e, sv);
+                    const T cf = sh->cq[q];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) r[k] += cf * sv[k];
+                }
             }
             ld4(g + e, gv);
 #pragma unroll
@@ -1354,6 +1498,7 @@ struct CellSolver {
         const TopoDev<T>& T_ = tp();
         const int n = T_.n, np = T_.n_pad, tid = threadIdx.x, NT = blockDim.x;
         if (nonfinite) status = NPFEM_CELL_NONFINITE;
+        if (crec) store_pairs();
         const T inv_h = T(1) / T_.h;
         Acc<T> ps[16];
         if (!nonfinite) {

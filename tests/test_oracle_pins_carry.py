@@ -135,3 +135,16 @@ def test_trajectory_with_carried_pairs_reaches_the_same_steps(m162):
     ia = np.mean([s.iterations for s in sa[4:]])
     ib = np.mean([s.iterations for s in sb[4:]])
     assert ib < ia, (ia, ib)
+
+
+def test_carry_rule_that_never_fires_is_the_plain_trajectory(m162):
+    # carry_max_iters below every step's iteration count: no solve starts from carried
+    # pairs, so the trajectory is the one without them, bit for bit
+    x = m162.rest.copy()
+    v = np.zeros_like(x)
+    f = W.shear_forces(x[None], m162.tris, np.array([500.0]))[0]
+    o = O.make_opts(tol=1e-9, max_iter=200)
+    xa, va, sa = m162.trajectory(x, v, f, 6, o, carry_pairs=False)
+    xb, vb, sb = m162.trajectory(x, v, f, 6, o, carry_pairs=True, carry_max_iters=-1)
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert [s.iterations for s in sa] == [s.iterations for s in sb]
