@@ -114,7 +114,12 @@ struct CellShared {
     T cq[kMaxHistory];
     long long item;          // work item handed to the block
     unsigned long long mbar; // tensor-core path: MMA completion barrier
-    unsigned need[16];       // tensor-core path: request flags of the cluster's blocks
+    // tensor-core path, asynchronous rounds: results of this block's request delivered
+    // (one arrival per block of the cluster), the requests pending at this block (bit d:
+    // block d), the batch being served, blocks of the cluster that have finished, and a
+    // broadcast word
+    unsigned long long dbar;
+    unsigned pend, batch, fin, flag;
     unsigned taddr;          // tensor-core path: tensor-memory base address
     // TF32 contraction (SIMT kernel): per stage of the streamed A^-1 ring, "chunk landed"
     // and "MMAs done reading it" barriers, and each stage's uses so far (phase parity)

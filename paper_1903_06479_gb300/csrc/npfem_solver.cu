@@ -939,32 +939,64 @@ struct CellSolver {
             l1 = XHI[n] == o1 ? XLO[n] : T(0);
             l2 = XHI[2 * n] == o2 ? XLO[2 * n] : T(0);
         }
-        for (int e = tid; e < N3; e += NT) {
-            const int c = e / np, i = e - c * np;
-            T xn = T(0), uy = T(0);
-            if (i < n) {
-                const T xv = x[c * n + i];
-                xn = xv - (c == 0 ? o0 : (c == 1 ? o1 : o2));
-                if (XLO) {
-                    const T lv = XHI[c * n + i] == xv ? XLO[c * n + i] : T(0);
-                    xn += lv - (c == 0 ? l0 : (c == 1 ? l1 : l2));
+        if (carry_in && !a->defer && threadIdx.x == 0) {
+            // the cell will most likely ask for a direction: bring its carried pairs into L2
+            // while the first evaluation runs
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(crec),
+                         "r"((uint32_t)(gd->carry_rec * (long long)sizeof(T)))
+                         : "memory");
+        }
+        // temporal warm start: u = u_y + (x_n - y_{n-1}), the cell's previous correction,
+        // folded into this pass (except with a temporal network or beta_D > 0)
+        const T* Hc = (hist && !(a->hist_ext && a->u0) && !T_.minv) ? a->hist_in + so : nullptr;
+        // U elements per thread at a time, every global load issued before the stores
+        // (the stores to shared memory would otherwise hold up the next element's loads)
+        constexpr int U = 4;
+        for (int e0 = tid; e0 < N3; e0 += U * NT) {
+            T xv[U], hv[U], lv[U], vv[U], fv[U], cv[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int e = e0 + q * NT, c = e / np, i = e - c * np;
+                xv[q] = hv[q] = lv[q] = vv[q] = fv[q] = cv[q] = T(0);
+                if (e < N3 && i < n) {
+                    const int gi = c * n + i;
+                    xv[q] = x[gi];
+                    if (XLO) {
+                        hv[q] = XHI[gi];
+                        lv[q] = XLO[gi];
+                    }
+                    if (eval_mode) {
+                        vv[q] = a->y[so + gi];
+                    } else {
+                        vv[q] = a->v[so + gi];
+                        fv[q] = a->f[so + gi];
+                    }
+                    if (Hc) cv[q] = Hc[gi];
                 }
-                if (eval_mode) {
-                    uy = a->y[so + c * n + i] - xv;
-                } else if (T_.minv) {
-                    // right-hand side h M v_n + h^2 F_ext of M~ (y - x_n), solved below
-                    const T vv = a->v[so + c * n + i], fv = a->f[so + c * n + i];
-                    ut[e] = h * __ldg(&T_.mass[i]) * vv + h * h * fv;
-                } else {
-                    const T vv = a->v[so + c * n + i], fv = a->f[so + c * n + i];
-                    uy = (h * vv + h * h * fv * __ldg(&T_.inv_mass[i])) * inv_ms;
-                }
-            } else if (T_.minv && !eval_mode) {
-                ut[e] = T(0);
             }
-            XN[e] = xn;
-            UYv[e] = uy;
-            u[e] = eval_mode ? T(0) : uy;
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int e = e0 + q * NT, c = e / np, i = e - c * np;
+                if (e >= N3) continue;
+                T xn = T(0), uy = T(0);
+                if (i < n) {
+                    xn = xv[q] - (c == 0 ? o0 : (c == 1 ? o1 : o2));
+                    if (XLO) xn += (hv[q] == xv[q] ? lv[q] : T(0)) - (c == 0 ? l0 : (c == 1 ? l1 : l2));
+                    if (eval_mode) {
+                        uy = vv[q] - xv[q];
+                    } else if (T_.minv) {
+                        // right-hand side h M v_n + h^2 F_ext of M~ (y - x_n), solved below
+                        ut[e] = h * __ldg(&T_.mass[i]) * vv[q] + h * h * fv[q];
+                    } else {
+                        uy = (h * vv[q] + h * h * fv[q] * __ldg(&T_.inv_mass[i])) * inv_ms;
+                    }
+                } else if (T_.minv && !eval_mode) {
+                    ut[e] = T(0);
+                }
+                XN[e] = xn;
+                UYv[e] = uy;
+                u[e] = eval_mode ? T(0) : uy + cv[q];
+            }
         }
         __syncthreads();
         if (T_.minv && !eval_mode) {
@@ -984,13 +1016,16 @@ struct CellSolver {
                 u[e] = i < n ? U0[c * n + i] : T(0);
             }
             __syncthreads();
-        } else if (hist) {
-            const T* Hc = a->hist_in + so;
+        } else if (hist && !Hc) {
+            // beta_D > 0: the correction on top of the dense first guess
+            const T* Hp = a->hist_in + so;
             for (int e = tid; e < N3; e += NT) {
                 const int c = e / np, i = e - c * np;
-                u[e] = i < n ? UYv[e] + Hc[c * n + i] : T(0);
+                u[e] = i < n ? UYv[e] + Hp[c * n + i] : T(0);
             }
             __syncthreads();
+        } else if (hist) {
+            // applied above
         } else if (ws && a->u0) {
             const T* U0 = a->u0 + so;
             for (int e = tid; e < N3; e += NT) {
@@ -1587,16 +1622,26 @@ struct CellSolver {
                 }
                 continue;
             }
+            // the global loads of all three coordinates first (the stores below would
+            // otherwise hold them up)
+            T xo3[3], hi3[3], lo3[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xo3[c] = x[c * n + i];
+                hi3[c] = lo_in ? XHI[c * n + i] : T(0);
+                lo3[c] = lo_in ? XLO[c * n + i] : T(0);
+            }
             T r[3];
             for (int c = 0; c < 3; ++c) r[c] = XN[c * np + i] + u[c * np + i] - xc[c];
             const T wr[3] = {w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2], w[0] * r[1] - w[1] * r[0]};
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const T uc = u[c * np + i];
                 const T vv = uc * inv_h;
                 v[c * n + i] = vv + kap * (vc[c] + wr[c] - vv);
-                const T xo = x[c * n + i];
+                const T xo = xo3[c];
                 if (XLO) {
-                    const T t = (lo_in && XHI[c * n + i] == xo ? XLO[c * n + i] : T(0)) + uc;
+                    const T t = (lo_in && hi3[c] == xo ? lo3[c] : T(0)) + uc;
                     const T sm = xo + t;
                     const T bv = sm - xo;
                     const T err = (xo - (sm - bv)) + (t - bv);
@@ -1762,17 +1807,21 @@ __global__ void __launch_bounds__(MAXT, 1) cell_kernel(const __grid_constant__ L
 // ---------------------------------------------------------------------------------
 // Tensor-core contraction: a cluster of ceil(n / 128) blocks, one block per SM, each
 // holding rows [128 r, 128 r + 128) of A^-1 (BF16) in tensor memory for the whole
-// launch.  A "round" applies A^-1 to the current request of every block of the
-// cluster at once:
-//   local work  -> each block with a request writes its vector (BF16) into row
-//                  3 r + c of the B operand of every block of the cluster (DSMEM);
-//   barrier     -> every block issues ceil(n/16) tcgen05.mma (M 128, N 16/32, K 16,
-//                  A from TMEM, B from shared memory, FP32 accumulate in TMEM),
-//                  reads its 128 result rows and writes them into the requesting
-//                  blocks' contraction vectors (DSMEM);
-//   barrier     -> results are in place.
-// Blocks without work still take part until every block of the cluster is idle, so
-// all blocks pass the same sequence of cluster barriers.
+// launch.  Blocks solve their cells independently; a contraction is a request that
+// every block of the cluster serves asynchronously:
+//   request -> the requesting block writes its vector (BF16) into rows 3 r + c of the
+//              B operand of every block (DSMEM) and sets its bit in every block's
+//              pending mask (release);
+//   serve   -> at its next poll point a block takes its pending mask (acquire),
+//              issues ceil(n/16) tcgen05.mma (M 128, N 16/32, K 16, A from TMEM, B
+//              from shared memory, FP32 accumulate in TMEM) for the whole batch,
+//              reads its 128 result rows and writes each requester's three columns
+//              into that requester's contraction vector (DSMEM), then arrives on the
+//              requester's delivery barrier (release);
+//   wait    -> the requester serves at its own poll points until all blocks of the
+//              cluster have delivered.
+// Poll points: while waiting for a result, and between the solver's phases.  A block
+// whose cells are done keeps serving until every block of the cluster is done.
 // ---------------------------------------------------------------------------------
 
 // Writes BF16(src) (3 rows of the cell, zero beyond n) into rows 3 rank + c of the B
@@ -1805,7 +1854,172 @@ __device__ void tc_post(const TopoDev<T>& tp, const T* src, const T* R, bool wit
     }
 }
 
-enum TcPhase { PH_NONE = 0, PH_DIR1, PH_DIR2, PH_FB1, PH_FB2 };
+// The asynchronous rounds of one block (see above).  Every method is called by all
+// threads of the block (control flow block-uniform).
+template <typename T, int NCOL>
+struct TcRounds {
+    CellShared<T>* sh;
+    const TopoDev<T>* tp;
+    unsigned char* bbuf;
+    T* GCv;
+    unsigned* err;
+    uint32_t tbase, dcol, idesc, sbo, bbase, rank, cs;
+    uint32_t nserv, nreq;
+
+    // Serves the requests pending at this block, if any.
+    __device__ void serve()
+    {
+        const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+        if (tid == 0) {
+            uint32_t b;
+            asm volatile("atom.acquire.cluster.shared::cluster.exch.b32 %0, [%1], 0;"
+                         : "=r"(b)
+                         : "r"(tc::smem_addr(&sh->pend))
+                         : "memory");
+            sh->batch = b;
+        }
+        __syncthreads();
+        const uint32_t batch = sh->batch;
+        if (batch == 0u) return;
+        const int kpad = tp->kpad, n = tp->n, np = tp->n_pad;
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < (kpad >> 4); ++ks) {
+                const uint64_t bd = tc::smem_desc(bbase + (uint32_t)ks * 256u, 128u, sbo);
+                const uint32_t ta = tbase + (uint32_t)(ks * 8);
+                const uint32_t acc = ks > 0;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tbase + dcol),
+                    "r"(ta), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc::smem_addr(&sh->mbar)));
+        }
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 22) && !done; ++it) {
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                : "=r"(done)
+                : "r"(tc::smem_addr(&sh->mbar)), "r"(nserv & 1u));
+        }
+        if (!done && tid == 0) atomicExch(err, 1u);  // reported to the host; results invalid
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (warp < 4) {
+            float dv[NCOL];
+            tc::tmem_ld<NCOL>(tbase + ((uint32_t)(32 * warp) << 16) + dcol, dv);
+            const int row = 128 * (int)rank + 32 * warp + lane;
+            if (row < n) {
+#pragma unroll
+                for (int d = 0; d < NCOL / 3 && d < 8; ++d) {
+                    if (!((batch >> d) & 1u)) continue;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const uint32_t loc = tc::smem_addr(GCv + c * np + row);
+                        tc::st_remote_f32(tc::map_rank(loc, (uint32_t)d), dv[3 * d + c]);
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid < (int)cs && ((batch >> tid) & 1u)) {
+            // the results written above (other threads, ordered by the barrier) are
+            // released with the arrival
+            const uint32_t rb = tc::map_rank(tc::smem_addr(&sh->dbar), (uint32_t)tid);
+            asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(rb) : "memory");
+        }
+        ++nserv;
+    }
+
+    // r = A^-1 src into GCv (BF16 operands, FP32 accumulation); with refine one more
+    // sweep r += A^-1 (src - H~ r).  tmp, keep: 3 x n_pad scratch.
+    __device__ void contract(const T* src, bool refine, T* tmp, T* keep)
+    {
+        request(src, false, tmp);
+        if (refine) {
+            const int N3 = 3 * tp->n_pad;
+            for (int e = threadIdx.x; e < N3; e += blockDim.x) keep[e] = GCv[e];
+            __syncthreads();
+            request(src, true, tmp);
+            for (int e = threadIdx.x; e < N3; e += blockDim.x) GCv[e] += keep[e];
+            __syncthreads();
+        }
+    }
+
+    // Posts src (or the refinement residual of src for r = GCv) and waits, serving, for
+    // the cs deliveries.
+    __device__ void request(const T* src, bool residual, T* tmp)
+    {
+        const int tid = threadIdx.x;
+        tc_post(*tp, src, GCv, residual, bbuf, rank, cs, tmp);
+        asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+        __syncthreads();
+        if (tid < (int)cs) {
+            const uint32_t pa = tc::map_rank(tc::smem_addr(&sh->pend), (uint32_t)tid);
+            asm volatile("red.release.cluster.shared::cluster.or.b32 [%0], %1;" ::"r"(pa), "r"(1u << rank) : "memory");
+        }
+        const uint32_t par = nreq & 1u;
+        bool ok = false;
+        for (int it = 0; it < (1 << 22); ++it) {
+            serve();
+            if (tid == 0) {
+                uint32_t d;
+                asm volatile(
+                    "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+                    "selp.u32 %0, 1, 0, p;\n}"
+                    : "=r"(d)
+                    : "r"(tc::smem_addr(&sh->dbar)), "r"(par)
+                    : "memory");
+                // the error word (global memory) only now and then: each read costs a round trip
+                sh->flag = d | ((it & 255) == 255 && *reinterpret_cast<volatile unsigned*>(err) != 0u ? 2u : 0u);
+            }
+            __syncthreads();
+            const uint32_t f = sh->flag;
+            if (f & 1u) {
+                ok = true;
+                break;
+            }
+            if (f & 2u) break;  // another block gave up: stop waiting
+        }
+        if (!ok && tid == 0) atomicExch(err, 1u);
+        ++nreq;
+    }
+
+    // The block's cells are done: tell every block, then serve until all are done.
+    __device__ void finish_and_drain()
+    {
+        const int tid = threadIdx.x;
+        __syncthreads();
+        if (tid < (int)cs) {
+            const uint32_t fa = tc::map_rank(tc::smem_addr(&sh->fin), (uint32_t)tid);
+            asm volatile("red.release.cluster.shared::cluster.add.u32 [%0], 1;" ::"r"(fa) : "memory");
+        }
+        bool ok = false;
+        for (int it = 0; it < (1 << 24); ++it) {
+            serve();
+            if (tid == 0) {
+                uint32_t f;
+                asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];"
+                             : "=r"(f)
+                             : "r"(tc::smem_addr(&sh->fin))
+                             : "memory");
+                sh->flag = (f >= cs ? 1u : 0u) |
+                           ((it & 255) == 255 && *reinterpret_cast<volatile unsigned*>(err) != 0u ? 2u : 0u);
+            }
+            __syncthreads();
+            const uint32_t f = sh->flag;
+            if (f & 1u) {
+                ok = true;
+                break;
+            }
+            if (f & 2u) break;
+        }
+        if (!ok && tid == 0) atomicExch(err, 1u);
+        // nothing is left pending: every request was delivered before its block finished
+    }
+};
 
 template <typename T, int NCOL>
 __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__ LaunchArgs<T> a)
@@ -1817,15 +2031,17 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
     unsigned char* bbuf = smem + kFixedSmem;  // B operand: NCOL rows x kpad BF16
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t rank = tc::cta_rank(), cs = (uint32_t)a.p.cluster;
-    const int n = tp.n, np = tp.n_pad, kpad = tp.kpad;
+    const int kpad = tp.kpad;
     const uint32_t acols = (uint32_t)(kpad >> 1);
     const uint32_t dcol = (acols + 31u) & ~31u;
 
-    // ---- set-up: zero B, flags, TMEM allocation, A^-1 rows of this block into TMEM
+    // ---- set-up: zero B, flags, barriers, TMEM allocation, A^-1 rows of this block into TMEM
     for (int q = tid; q < NCOL * kpad / 8; q += blockDim.x) reinterpret_cast<uint4*>(bbuf)[q] = make_uint4(0, 0, 0, 0);
-    if (tid < 16) sh->need[tid] = 0u;
     if (tid == 0) {
+        sh->pend = 0u;
+        sh->fin = 0u;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&sh->mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::smem_addr(&sh->dbar)), "r"(cs));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -1851,133 +2067,51 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    tc::cluster_sync();
+    tc::cluster_sync();  // every block's barriers and flags are initialised
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCOL >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    const uint32_t lbo = 128u, sbo = (uint32_t)(kpad >> 3) * 128u;
-    const uint32_t bbase = tc::smem_addr(bbuf);
-    const bool refine = a.p.refine != 0;
 
     CellSolver<T> S;
     S.bind(a, gd, smem);
-    int phase = PH_NONE;
-    bool have_result = false, exhausted = false;
-    uint32_t round = 0;
-    for (;;) {
-        // ---- local work up to the next request (or idle)
-        bool need = false;
-        for (;;) {
-            if (phase == PH_NONE) {
-                const long long item = exhausted ? -1 : next_item(a, smem);
-                if (item < 0) {
-                    exhausted = true;
-                    break;
-                }
-                S.begin(item, item);
-                const bool wants = S.wants_direction();
-                if (a.need && wants && tid == 0) atomicAdd(a.need, 1u);
-            } else if (have_result) {
-                have_result = false;
-                if ((phase == PH_DIR1 || phase == PH_FB1) && refine) {
-                    // keep r1, request A^-1 (src - H~ r1)
-                    const int N3 = 3 * np;
-                    for (int e = tid; e < N3; e += blockDim.x) S.ut[e] = S.GCv[e];
-                    __syncthreads();
-                    tc_post(tp, phase == PH_DIR1 ? S.Dv : S.g, S.GCv, true, bbuf, rank, cs, S.WRv);
-                    phase = phase == PH_DIR1 ? PH_DIR2 : PH_FB2;
-                    need = true;
-                    break;
-                }
-                if (phase == PH_DIR2 || phase == PH_FB2) {
-                    const int N3 = 3 * np;
-                    for (int e = tid; e < N3; e += blockDim.x) S.GCv[e] += S.ut[e];
-                    __syncthreads();
-                }
-                if (phase == PH_DIR1 || phase == PH_DIR2) {
-                    S.second_loop();
-                    if (!S.descent()) {
-                        S.count = 0;
-                        tc_post(tp, S.g, S.GCv, false, bbuf, rank, cs, S.WRv);
-                        phase = PH_FB1;
-                        need = true;
-                        break;
-                    }
-                } else {
-                    S.negate_direction();
-                }
-                if (!S.line_search_update()) {
-                    S.finish();
-                    phase = PH_NONE;
-                    continue;
-                }
-            }
-            if (!S.wants_direction()) {
-                S.finish();
-                phase = PH_NONE;
-                continue;
-            }
-            S.first_loop();
-            tc_post(tp, S.Dv, S.GCv, false, bbuf, rank, cs, S.WRv);
-            phase = PH_DIR1;
-            need = true;
-            break;
-        }
-        // announce the request flag to every block of the cluster
-        if (tid < (int)cs) tc::st_remote_u32(tc::map_rank(tc::smem_addr(&sh->need[rank]), (uint32_t)tid), need ? 1u : 0u);
-        asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
-        tc::cluster_sync();
-        uint32_t any = 0;
-        for (uint32_t d = 0; d < cs; ++d) any |= sh->need[d];
-        if (!any) break;
+    TcRounds<T, NCOL> R;
+    R.sh = sh;
+    R.tp = &tp;
+    R.bbuf = bbuf;
+    R.GCv = S.GCv;
+    R.err = &a.work[2];
+    R.tbase = tbase;
+    R.dcol = dcol;
+    R.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCOL >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    R.sbo = (uint32_t)(kpad >> 3) * 128u;
+    R.bbase = tc::smem_addr(bbuf);
+    R.rank = rank;
+    R.cs = cs;
+    R.nserv = 0u;
+    R.nreq = 0u;
+    const bool refine = a.p.refine != 0;
 
-        // ---- the round: MMAs on this block's row block for every request
-        if (tid == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int ks = 0; ks < (kpad >> 4); ++ks) {
-                const uint64_t bd = tc::smem_desc(bbase + (uint32_t)ks * 256u, lbo, sbo);
-                const uint32_t ta = tbase + (uint32_t)(ks * 8);
-                const uint32_t acc = ks > 0;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tbase + dcol),
-                    "r"(ta), "l"(bd), "r"(idesc), "r"(acc));
+    for (;;) {
+        R.serve();
+        const long long item = next_item(a, smem);
+        if (item < 0) break;
+        S.begin(item, item);
+        const bool wants = S.wants_direction();
+        if (a.need && wants && tid == 0) atomicAdd(a.need, 1u);
+        while (S.wants_direction()) {
+            R.serve();
+            S.first_loop();
+            R.contract(S.Dv, refine, S.WRv, S.ut);  // r = H0 q
+            S.second_loop();
+            if (!S.descent()) {
+                // not a descent direction: drop the history, d = -H~^-1 g
+                S.count = 0;
+                R.contract(S.g, refine, S.WRv, S.ut);
+                S.negate_direction();
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                tc::smem_addr(&sh->mbar)));
+            if (!S.line_search_update()) break;
         }
-        uint32_t done = 0;
-        for (int it = 0; it < (1 << 22) && !done; ++it) {
-            asm volatile(
-                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                : "=r"(done)
-                : "r"(tc::smem_addr(&sh->mbar)), "r"(round & 1u));
-        }
-        if (!done && tid == 0) atomicExch(&a.work[2], 1u);  // reported to the host; results invalid
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (warp < 4) {
-            float dv[NCOL];
-            tc::tmem_ld<NCOL>(tbase + ((uint32_t)(32 * warp) << 16) + dcol, dv);
-            const int row = 128 * (int)rank + 32 * warp + lane;
-            if (row < n) {
-#pragma unroll
-                for (int d = 0; d < NCOL / 3 && d < 8; ++d) {
-                    if (d >= (int)cs || !sh->need[d]) continue;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const uint32_t loc = tc::smem_addr(S.GCv + c * np + row);
-                        tc::st_remote_f32(tc::map_rank(loc, (uint32_t)d), dv[3 * d + c]);
-                    }
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        tc::cluster_sync();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        have_result = need;
-        ++round;
+        S.finish();
     }
+    R.finish_and_drain();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     tc::cluster_sync();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
