@@ -870,6 +870,7 @@ struct CellSolver {
     // the pairs of the cell's last solve; carry_in: not yet loaded in this step
     T* crec;
     bool carry_valid, carry_in;
+    bool carry_early;  // begin issued the carried pairs' copies (load_pairs only waits)
     T ccount;  // the record's pair count, read in begin (its latency hidden by the evaluation)
     T clast;   // the record's iteration count of the cell's last step
     // history vectors that do not fit in shared memory live in the record (they may be
@@ -939,12 +940,17 @@ struct CellSolver {
             l1 = XHI[n] == o1 ? XLO[n] : T(0);
             l2 = XHI[2 * n] == o2 ? XLO[2 * n] : T(0);
         }
-        if (carry_in && !a->defer && threadIdx.x == 0) {
-            // the cell will most likely ask for a direction: bring its carried pairs into L2
-            // while the first evaluation runs
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(crec),
-                         "r"((uint32_t)(gd->carry_rec * (long long)sizeof(T)))
-                         : "memory");
+        carry_early = carry_in && !a->defer;
+        if (carry_early) {
+            // the cell will most likely ask for a direction: its carried pairs travel while
+            // the first evaluation runs (the record into L2; the ring slots held in shared
+            // memory and the inner products by asynchronous copies, whatever the record's
+            // count; load_pairs waits for them)
+            if (threadIdx.x == 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(crec),
+                             "r"((uint32_t)(gd->carry_rec * (long long)sizeof(T)))
+                             : "memory");
+            issue_pair_copies();
         }
         // temporal warm start: u = u_y + (x_n - y_{n-1}), the cell's previous correction,
         // folded into this pass (except with a temporal network or beta_D > 0)
@@ -1157,21 +1163,17 @@ struct CellSolver {
     // asynchronous 16-byte copies, all of a thread's in flight at once.  s_i^T g at the
     // current iterate takes one block reduction.  Called at the step's first direction
     // request, so a cell accepted at its first iterate reads nothing.
-    __device__ void load_pairs()
+    // Asynchronous copies of the record's ring slots held in shared memory (all m slots,
+    // valid or not) and of its inner products.  The caller waits (cp.async.wait_all)
+    // before reading them or reusing the buffers.
+    __device__ void issue_pair_copies()
     {
-        carry_in = false;
         const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x, Mm = M;
-        if (!(ccount >= T(1)) || !(clast <= T(kCarryMaxIters))) return;
-        const int cnt = ccount < T(Mm) ? (int)ccount : Mm;
-        const T hv = crec[1];
-        const int hd = hv >= T(0) && hv < T(Mm) ? (int)hv : 0;
         const T* V = crec + carry_head_elems(Mm);
-        for (int q = 0; q < 2 * cnt; ++q) {
-            const int i = (hd - 1 - (q >> 1) + Mm) % Mm;
-            const int r = (q & 1) ? Mm + i : i;  // s then y of each valid slot
+        for (int r = 0; r < 2 * Mm; ++r) {
             if (gd->loc[V_SBASE + r] < 0) continue;  // used in place
             const T* src = V + (long long)r * N3;
-            T* dst = hist(V_SBASE + r);
+            T* dst = vec_ptr(*gd, smem, slot, V_SBASE + r);
             for (int e = 4 * tid; e < N3; e += 4 * NT) {
 #pragma unroll
                 for (int b = 0; b < (int)sizeof(T) / 4; ++b)
@@ -1181,8 +1183,39 @@ struct CellSolver {
                                  : "memory");
             }
         }
-        for (int k = tid; k < Mm * Mm; k += NT) sh->SY[k / Mm][k % Mm] = crec[4 + k];
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        for (int k = tid; k < Mm * Mm; k += NT) {
+            if constexpr (sizeof(T) == 4)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                                 (uint32_t)__cvta_generic_to_shared(&sh->SY[k / Mm][k % Mm])),
+                             "l"(__cvta_generic_to_global(crec + 4 + k))
+                             : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                                 (uint32_t)__cvta_generic_to_shared(&sh->SY[k / Mm][k % Mm])),
+                             "l"(__cvta_generic_to_global(crec + 4 + k))
+                             : "memory");
+        }
+    }
+
+    __device__ void load_pairs()
+    {
+        carry_in = false;
+        const int N3 = 3 * tp().n_pad, tid = threadIdx.x, NT = blockDim.x, Mm = M;
+        const bool issued = carry_early;
+        if (issued) {
+            // the copies begin issued land before any ring slot is written
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+            carry_early = false;
+        }
+        if (!(ccount >= T(1)) || !(clast <= T(kCarryMaxIters))) return;
+        const int cnt = ccount < T(Mm) ? (int)ccount : Mm;
+        const T hv = crec[1];
+        const int hd = hv >= T(0) && hv < T(Mm) ? (int)hv : 0;
+        if (!issued) {
+            issue_pair_copies();
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        }
         head = hd;
         count = cnt;
         __syncthreads();
@@ -1533,6 +1566,11 @@ struct CellSolver {
         const TopoDev<T>& T_ = tp();
         const int n = T_.n, np = T_.n_pad, tid = threadIdx.x, NT = blockDim.x;
         if (nonfinite) status = NPFEM_CELL_NONFINITE;
+        if (carry_early) {
+            // copies issued in begin that no direction request waited for
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+        }
         if (crec) store_pairs();
         const T inv_h = T(1) / T_.h;
         Acc<T> ps[16];
