@@ -149,6 +149,10 @@ __device__ __forceinline__ T prm(double d, float f)
 // Sums K compensated accumulators over the block.  Thread 0 writes the totals to
 // sh->out[] and then runs epi(sh) before the closing barrier, so every thread sees
 // the totals and whatever the epilogue derived from them.
+// Reductions of at least this many values run their second stage on all warps (one
+// value per warp) instead of on warp 0 alone, at the price of one more barrier.
+constexpr int kSpreadReduce = 8;
+
 struct NoEpi {
     template <typename S>
     __device__ __forceinline__ void operator()(S*) const {}
@@ -176,7 +180,28 @@ __device__ __forceinline__ void block_reduce(Acc<T> (&a)[K], unsigned char* smem
         }
     }
     __syncthreads();
-    if (w == 0) {
+    if constexpr (K >= kSpreadReduce) {
+        // value k across the warps' partials on warp k mod nw (the same tree as below)
+        for (int k = w; k < K; k += nw) {
+            Acc<T> b;
+            if (lane < nw) {
+                b.hi = red[(lane * K + k) * 2];
+                b.lo = red[(lane * K + k) * 2 + 1];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T h2 = __shfl_xor_sync(kFull, b.hi, o);
+                const T l2 = __shfl_xor_sync(kFull, b.lo, o);
+                b.merge(h2, l2);
+            }
+            if (lane == 0) {
+                sh->out[k] = b.hi;
+                sh->outlo[k] = b.lo;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) epi(sh);
+    } else if (w == 0) {
         Acc<T> b[K];
 #pragma unroll
         for (int k = 0; k < K; ++k)
@@ -234,7 +259,35 @@ __device__ __forceinline__ void block_reduce_cp(Acc<T> (&a)[KC], T (&p)[KP], uns
         for (int k = 0; k < KP; ++k) red[w * W + 2 * KC + k] = p[k];
     }
     __syncthreads();
-    if (w == 0) {
+    if constexpr (KC + KP >= kSpreadReduce) {
+        // value v across the warps' partials on warp v mod nw (the same tree as below)
+        for (int v = w; v < KC + KP; v += nw) {
+            if (v < KC) {
+                Acc<T> b;
+                if (lane < nw) {
+                    b.hi = red[lane * W + 2 * v];
+                    b.lo = red[lane * W + 2 * v + 1];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const T h2 = __shfl_xor_sync(kFull, b.hi, o);
+                    const T l2 = __shfl_xor_sync(kFull, b.lo, o);
+                    b.merge(h2, l2);
+                }
+                if (lane == 0) {
+                    sh->out[v] = b.hi;
+                    sh->outlo[v] = b.lo;
+                }
+            } else {
+                T q = lane < nw ? red[lane * W + 2 * KC + (v - KC)] : T(0);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
+                if (lane == 0) sh->out[v] = q;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) epi(sh);
+    } else if (w == 0) {
         Acc<T> b[KC];
         T q[KP];
 #pragma unroll
@@ -289,7 +342,17 @@ __device__ __forceinline__ void block_sum(T (&p)[K], unsigned char* smem, Epi ep
         for (int k = 0; k < K; ++k) red[w * K + k] = p[k];
     }
     __syncthreads();
-    if (w == 0) {
+    if constexpr (K >= kSpreadReduce) {
+        // value k across the warps' partials on warp k mod nw (the same tree as below)
+        for (int k = w; k < K; k += nw) {
+            T q = lane < nw ? red[lane * K + k] : T(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
+            if (lane == 0) sh->out[k] = q;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) epi(sh);
+    } else if (w == 0) {
         T q[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) q[k] = lane < nw ? red[lane * K + k] : T(0);

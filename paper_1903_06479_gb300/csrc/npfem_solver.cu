@@ -874,8 +874,13 @@ struct CellSolver {
     T ccount;  // the record's pair count, read in begin (its latency hidden by the evaluation)
     T clast;   // the record's iteration count of the cell's last step
     // history vectors that do not fit in shared memory live in the record (they may be
-    // carried to the next step) rather than in the block's slot
-    bool ring_in_record;
+    // carried to the next step) rather than in the block's slot, unless the record's
+    // pairs are not to be carried (the last solve took more than kCarryMaxIters
+    // iterations); evaluated where used, after the header has arrived
+    __device__ bool ring_in_record() const
+    {
+        return crec && M > 0 && (!carry_valid || clast <= T(kCarryMaxIters));
+    }
 
     __device__ const TopoDev<T>& tp() const { return gd->topo; }
     // A solver vector; with carried pairs, a history vector that does not fit in shared
@@ -883,7 +888,7 @@ struct CellSolver {
     // block's global slot, so that the pairs persist without a copy.
     __device__ T* hist(int v) const
     {
-        if (ring_in_record && v >= V_SBASE && gd->loc[v] < 0)
+        if (ring_in_record() && v >= V_SBASE && gd->loc[v] < 0)
             return crec + carry_head_elems(M) + (long long)(v - V_SBASE) * 3 * tp().n_pad;
         return vec_ptr(*gd, smem, slot, v);
     }
@@ -925,9 +930,11 @@ struct CellSolver {
         crec = (!eval_mode && a->carry) ? a->carry + gd->carry_off + cell * gd->carry_rec : nullptr;
         carry_valid = crec && hist;
         carry_in = carry_valid && M > 0;
+        // global words read here come back while the loads below are issued (nothing is
+        // stored in between): the record's header, the listed-cell count, vertex 0
         ccount = carry_in ? crec[0] : T(0);
         clast = carry_in ? crec[2] : T(0);
-        ring_in_record = crec && M > 0 && (!carry_in || clast <= T(kCarryMaxIters));
+        const unsigned only_prev = a->only ? a->only[2] : 0u;
         const T* x = a->x + so;
         // compensated positions: x_n = x + residue while x holds exactly the value the
         // last step stored (each coordinate checked), else x alone
@@ -936,9 +943,11 @@ struct CellSolver {
         const T o0 = x[0], o1 = x[n], o2 = x[2 * n];
         T l0 = T(0), l1 = T(0), l2 = T(0);
         if (XLO) {
-            l0 = XHI[0] == o0 ? XLO[0] : T(0);
-            l1 = XHI[n] == o1 ? XLO[n] : T(0);
-            l2 = XHI[2 * n] == o2 ? XLO[2 * n] : T(0);
+            const T h0 = XHI[0], h1 = XHI[n], h2 = XHI[2 * n];
+            const T r0 = XLO[0], r1 = XLO[n], r2 = XLO[2 * n];
+            l0 = h0 == o0 ? r0 : T(0);
+            l1 = h1 == o1 ? r1 : T(0);
+            l2 = h2 == o2 ? r2 : T(0);
         }
         carry_early = carry_in && !a->defer;
         if (carry_early) {
@@ -1083,7 +1092,7 @@ struct CellSolver {
             __syncthreads();
         }
         // a listed cell was evaluated once by the first-iterate pass when that pass evaluated
-        evals = a->only && 2ll * (long long)a->only[2] <= a->total_cells ? 2 : 1;
+        evals = a->only && 2ll * (long long)only_prev <= a->total_cells ? 2 : 1;
         if (ws == 2) {
             // keep the learned guess only if it lowers g: evaluate at y (trial buffers) first
             for (int e = tid; e < N3; e += NT) ut[e] = UYv[e];
@@ -1274,7 +1283,7 @@ struct CellSolver {
         for (int q = 0; q < 2 * cnt; ++q) {
             const int i = hslot(q >> 1);
             const int r = (q & 1) ? Mm + i : i;
-            if (ring_in_record && gd->loc[V_SBASE + r] < 0) continue;  // already in the record
+            if (ring_in_record() && gd->loc[V_SBASE + r] < 0) continue;  // already in the record
             const T* src = hist(V_SBASE + r);
             T* dst = V + (long long)r * N3;
             for (int e = 4 * tid; e < N3; e += 4 * NT) {
