@@ -871,6 +871,7 @@ struct CellSolver {
     T* crec;
     bool carry_valid, carry_in;
     bool carry_early;  // begin issued the carried pairs' copies (load_pairs only waits)
+    unsigned dirty;    // ring slots written by this solve (the others match the record)
     T ccount;  // the record's pair count, read in begin (its latency hidden by the evaluation)
     T clast;   // the record's iteration count of the cell's last step
     // history vectors that do not fit in shared memory live in the record (they may be
@@ -968,14 +969,15 @@ struct CellSolver {
         // (the stores to shared memory would otherwise hold up the next element's loads)
         constexpr int U = 4;
         for (int e0 = tid; e0 < N3; e0 += U * NT) {
-            T xv[U], hv[U], lv[U], vv[U], fv[U], cv[U];
+            T xv[U], hv[U], lv[U], vv[U], fv[U], cv[U], mv[U];
 #pragma unroll
             for (int q = 0; q < U; ++q) {
                 const int e = e0 + q * NT, c = e / np, i = e - c * np;
-                xv[q] = hv[q] = lv[q] = vv[q] = fv[q] = cv[q] = T(0);
+                xv[q] = hv[q] = lv[q] = vv[q] = fv[q] = cv[q] = mv[q] = T(0);
                 if (e < N3 && i < n) {
                     const int gi = c * n + i;
                     xv[q] = x[gi];
+                    mv[q] = T_.minv ? __ldg(&T_.mass[i]) : __ldg(&T_.inv_mass[i]);
                     if (XLO) {
                         hv[q] = XHI[gi];
                         lv[q] = XLO[gi];
@@ -1001,9 +1003,9 @@ struct CellSolver {
                         uy = vv[q] - xv[q];
                     } else if (T_.minv) {
                         // right-hand side h M v_n + h^2 F_ext of M~ (y - x_n), solved below
-                        ut[e] = h * __ldg(&T_.mass[i]) * vv[q] + h * h * fv[q];
+                        ut[e] = h * mv[q] * vv[q] + h * h * fv[q];
                     } else {
-                        uy = (h * vv[q] + h * h * fv[q] * __ldg(&T_.inv_mass[i])) * inv_ms;
+                        uy = (h * vv[q] + h * h * fv[q] * mv[q]) * inv_ms;
                     }
                 } else if (T_.minv && !eval_mode) {
                     ut[e] = T(0);
@@ -1124,6 +1126,7 @@ struct CellSolver {
         status = NPFEM_CELL_OK;
         head = 0;
         count = 0;
+        dirty = 0u;
         if (eval_mode) {
             for (int e = tid; e < 3 * n; e += NT) {
                 const int c = e / n, i = e - c * n;
@@ -1280,9 +1283,12 @@ struct CellSolver {
         }
         const int cnt = count;
         T* V = crec + carry_head_elems(Mm);
+        // a slot loaded from the record and not written since still matches it
+        const unsigned todo = carry_valid && ring_in_record() ? dirty : ~0u;
         for (int q = 0; q < 2 * cnt; ++q) {
             const int i = hslot(q >> 1);
             const int r = (q & 1) ? Mm + i : i;
+            if (!((todo >> i) & 1u)) continue;
             if (ring_in_record() && gd->loc[V_SBASE + r] < 0) continue;  // already in the record
             const T* src = hist(V_SBASE + r);
             T* dst = V + (long long)r * N3;
@@ -1537,6 +1543,7 @@ struct CellSolver {
                 if (c->push) c->sg[hd] = o[4];
             });
             if (sh->push) {
+                dirty |= 1u << head;
                 T* S = hist(V_SBASE + head);
                 T* Y = hist(V_SBASE + M + head);
                 for (int e = 4 * tid; e < N3; e += 4 * NT) {
