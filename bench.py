@@ -59,7 +59,14 @@ METRIC = "RBC-steps/s (642-vtx cells, equal accuracy), chosen vs plain form, % r
 # DRAM bytes (read + write) of the solver launches of one step, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of this code, keyed by
 # (cells, precision, temporal warm start, noise redrawn).  Emptied when a kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # the three solver launches of one timed step (first-iterate pass, cluster kernel,
+    # idle-SM SIMT blocks), mean over the 20 timed steps of
+    #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
+    #       -k regex:cell_kernel --csv --log-file dram.csv python bench.py --steps 20 --warmup 5 --legs none \
+    #       --no-cpu --no-plain --no-e2e --warmstart none --autotune 0
+    (1024, "bf16", 2, 0): 138016960,
+}
 DT = 0.1
 N_VERTS = 642
 
@@ -449,11 +456,14 @@ def roofline(pk, pk_kind, groups_n, leg, m, history, cells_by_group, kernel_name
 
 
 def compare_leg(N, W, torch, name, pops, counts, args, flush, ws_params, local, pk, pk_kind, fpools=None,
-                refine=0, plain=True, mat=None, ibm=False, precision=None):
-    """Chosen form and plain FP32 path on the same cells, steps and residual tolerance."""
+                refine=0, plain=True, mat=None, ibm=False, precision=None, autotune=True):
+    """Chosen form and plain FP32 path on the same cells, steps and residual tolerance.
+    autotune=False keeps the default launch shape (for BF16: the tensor-core clusters),
+    so that a leg measures the form it names."""
     mat = mat or {}
     prec = precision or args.precision
-    hs, shapes = make_chosen(N, W, pops, counts, prec, args.history, refine, ws_params, local, torch, **mat)
+    hs, shapes = make_chosen(N, W, pops, counts, prec, args.history, refine, ws_params, local, torch,
+                             autotune=autotune, **mat)
     ffn, lat_info = ibm_force_fn(N, W, torch, hs, counts) if ibm else (None, None)
     ch = device_leg(N, W, hs, pops, counts, args.steps, args.warmup, torch, flush, kernel_times=True,
                     graph=bool(args.graph), fpools=fpools, force_fn=ffn)
@@ -577,8 +587,10 @@ def main():
                                     fpools=[noise], ibm=True)
         legs["regen"]["forces"] = IBM_FORCES
     if "refine1" in want and args.precision == "bf16":
+        # the tuner would take the SIMT FP32 contraction here (a refinement sweep doubles
+        # the cluster requests); the leg measures the tensor-core form with the sweep
         legs["refine1"] = compare_leg(N, W, torch, "refine1", [pop], [cells], args, flush, P, local, pk, pk_kind,
-                                      refine=1, plain=False)
+                                      refine=1, plain=False, autotune=False)
         legs["refine1"]["form"] = "chosen form with one refinement sweep of the tensor-core contraction"
     if want & {"c4", "c4_tf32", "c4_bf16_refine1"}:
         p4 = W.population(N_VERTS, 16384, seed=3 + rank, forces="shear", gamma_fixed=1000.0, noise_pN=2.0)
@@ -595,7 +607,8 @@ def main():
             legs["c4_tf32"]["workload"] = w4
         if "c4_bf16_refine1" in want:
             legs["c4_bf16_refine1"] = compare_leg(N, W, torch, "c4_bf16_refine1", [p4], [16384], args, flush, P,
-                                                  local, pk, pk_kind, refine=1, plain=False, precision="bf16")
+                                                  local, pk, pk_kind, refine=1, plain=False, precision="bf16",
+                                                  autotune=False)
             legs["c4_bf16_refine1"]["form"] = "BF16 tensor-core A^-1 contraction (clusters) + one refinement sweep"
             legs["c4_bf16_refine1"]["workload"] = w4
         del p4
