@@ -510,10 +510,9 @@ int step_groups(npfem_handle* const* meshes, int n_groups, const int32_t* cells_
                 NPFEM_CUDA(cudaMemsetAsync(hg->defer, 0, 3 * sizeof(unsigned int), s));
             }
             if (hin && (size_t)cg + 3 <= hg->defer_len) {
-                // along a trajectory most cells are accepted at the first iterate: a SIMT
-                // launch on every SM evaluates each cell there and finishes those, and the
-                // cluster kernel takes only the rest (in lockstep rounds, cells without
-                // iterations would hold up the blocks that need a contraction)
+                // along a trajectory many cells are accepted at the first iterate: a SIMT
+                // launch on every SM (the clusters' idle SMs included) evaluates each cell
+                // there and finishes those, and the cluster kernel takes only the rest
                 NPFEM_CUDA(cudaMemcpyAsync(hg->defer + 2, hg->defer + 1, sizeof(unsigned int), cudaMemcpyDeviceToDevice, s));
                 NPFEM_CUDA(cudaMemsetAsync(hg->defer, 0, 2 * sizeof(unsigned int), s));
                 int rc = run_cells<float>(&hg, 1, &cg, xg, vg, fg, nullptr, nullptr, nullptr, sg, 0, s,

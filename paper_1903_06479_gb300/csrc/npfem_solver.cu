@@ -2175,7 +2175,8 @@ __global__ void __launch_bounds__(512, 1) cell_kernel_tc(const __grid_constant__
 }  // namespace
 
 // SIMT kernel variants by block size: 512 threads (128 registers) and, for FP32, 640
-// threads (96 registers; fills the vertex passes of 642-vertex cells in one round).
+// threads (96 registers; 20 warps, the triangle pass of a 642-vertex cell in two rounds
+// instead of three).
 template <typename T>
 cudaError_t set_cell_kernel_smem(int bytes)
 {
