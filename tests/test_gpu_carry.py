@@ -156,3 +156,34 @@ def test_carried_pairs_reset_with_a_new_layout(npfem):
     h0 = make_handle(npfem, 642, "fp32", tol=1e-6, warm_history=0)
     xb, vb, sb = gpu_step_device(h0, q["x"], q["v"], q["f"])
     assert np.array_equal(xa, xb) and np.array_equal(sa["iterations"], sb["iterations"])
+
+
+def test_carried_pairs_left_out_while_solves_take_more_than_three_iterations(npfem):
+    # noise redrawn every step: every solve takes 4 or more iterations, so the rule never
+    # loads the carried pairs and the trajectory is the one without them, bit for bit
+    # (compared while every cell's last solve took more than 3 iterations)
+    import torch
+    cells = 8
+    p = population32(642, cells, seed=93, forces="shear", noise_pN=0.5)
+    rng = np.random.default_rng(5)
+    draws = [W.to_soa(p["f_shear"] + rng.normal(0, 0.5, p["x"].shape)) for _ in range(10)]
+    out = {}
+    for wh in (1, 2):
+        h = make_handle(npfem, 642, "fp32", tol=1e-6, warm_history=wh)
+        xs, vs = (torch.tensor(W.to_soa(p[k]), dtype=torch.float32, device="cuda") for k in ("x", "v"))
+        st = torch.zeros((cells, 32), dtype=torch.uint8, device="cuda")
+        xk, its = [], []
+        for f in draws:
+            fs = torch.tensor(f, dtype=torch.float32, device="cuda")
+            npfem.step([h], [cells], xs, vs, fs, DT, stats=st)
+            s = st.cpu().numpy().view(npfem.CELL_STATS_DTYPE).reshape(cells)
+            assert (s["status"] == 0).all()
+            xk.append(xs.cpu().numpy().copy())
+            its.append(s["iterations"].copy())
+        out[wh] = (xk, its)
+    k = 0
+    while k < len(draws) and (k == 0 or (out[1][1][k - 1] > 3).all()):
+        assert np.array_equal(out[1][0][k], out[2][0][k]), k
+        assert np.array_equal(out[1][1][k], out[2][1][k]), k
+        k += 1
+    assert k >= 5, (k, [i.min() for i in out[1][1]])
