@@ -220,10 +220,15 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
 int npfem_step_static(npfem_handle* const* meshes, int n_groups, const int32_t* cells_per_group, void* x, void* v,
                       const void* f_ext, double dt, void* stream, npfem_cell_stats* stats);
 
-/* Same as npfem_step for one handle with HOST buffers: copies x, v, f_ext (host,
-   SoA, same element type) to library-owned device buffers, steps, and copies x, v
-   and (if stats_host != NULL) the per-cell stats back; returns after the copies
-   completed. Errors as npfem_step, plus OOM. */
+/* Same as npfem_step for one handle with HOST buffers x, v, f_ext (SoA, same element
+   type; x, v updated in place) and, if stats_host != NULL, host per-cell stats;
+   returns after the step's results are in the host buffers.  Pinned host buffers
+   that are mapped into the device's address space (cudaHostAlloc, or cudaHostRegister
+   with mapping) are stepped in place: the solver kernels read x, v, F_ext and write x,
+   v and the stats over the host link while they compute (on a coherent CPU-GPU link
+   this overlaps the transfer with the step).  Any other host buffer is copied to
+   library-owned device buffers before the step and back after it.  The temporal warm
+   start continues a trajectory either way.  Errors as npfem_step, plus OOM. */
 int npfem_step_host(npfem_handle* h, int n_cells, void* x_host, void* v_host, const void* f_host, double dt,
                     void* stream, npfem_cell_stats* stats_host);
 

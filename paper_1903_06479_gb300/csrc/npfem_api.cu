@@ -1080,6 +1080,18 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
     return rc;
 }
 
+// The device address of a pinned host buffer mapped into the current device's address
+// space (cudaHostAlloc, or cudaHostRegister with mapping), or null for any other pointer.
+static void* mapped_host(void* p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // not a pointer the runtime knows: clear the error, copy instead
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int npfem_step_host(npfem_handle* h, int n_cells, void* x_host, void* v_host, const void* f_host, double dt,
                     void* stream, npfem_cell_stats* stats_host)
 {
@@ -1108,15 +1120,34 @@ int npfem_step_host(npfem_handle* h, int n_cells, void* x_host, void* v_host, co
         }
     }
     if (n_cells == 0) return 0;
-    NPFEM_CUDA(cudaMemcpyAsync(h->hx, x_host, bytes, cudaMemcpyHostToDevice, s));
-    NPFEM_CUDA(cudaMemcpyAsync(h->hv, v_host, bytes, cudaMemcpyHostToDevice, s));
-    NPFEM_CUDA(cudaMemcpyAsync(h->hf, f_host, bytes, cudaMemcpyHostToDevice, s));
     int32_t cells = n_cells;
     npfem_handle* hs[1] = {h};
     // a synchronous step starts on an idle GPU, where the idle-SM blocks can be placed
     // before the clusters and cost cluster slots (measured: slower), so it runs without
     const int fill = h->opts.fill_idle_sms;
     h->opts.fill_idle_sms = 0;
+    // pinned host buffers mapped into the device's address space are stepped in place:
+    // the solver's loads at the start of a cell and its stores at the end move x, v and
+    // F_ext over the host link while other cells compute, instead of copies before and
+    // after the step
+    void* xd = mapped_host(x_host);
+    void* vd = mapped_host(v_host);
+    void* fd = mapped_host(const_cast<void*>(f_host));
+    void* sd = stats_host ? mapped_host(stats_host) : nullptr;
+    if (xd && vd && fd && (!stats_host || sd)) {
+        int rc = npfem_step(hs, 1, &cells, xd, vd, fd, dt, stream, static_cast<npfem_cell_stats*>(sd));
+        h->opts.fill_idle_sms = fill;
+        if (rc) return rc;
+        NPFEM_CUDA(cudaStreamSynchronize(s));
+        return 0;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->hx, x_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hv, v_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hf, f_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        h->opts.fill_idle_sms = fill;
+        return fail(NPFEM_ERR_CUDA, std::string("npfem_step_host copies in: ") + cudaGetErrorString(e));
+    }
     int rc = npfem_step(hs, 1, &cells, h->hx, h->hv, h->hf, dt, stream, stats_host ? h->hstats : nullptr);
     h->opts.fill_idle_sms = fill;
     if (rc) return rc;

@@ -200,6 +200,27 @@ def test_step_host_matches_device(npfem):
     assert np.array_equal(st["iterations"], sg["iterations"])
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_step_host_pinned_in_place_matches_device(npfem, prec):
+    # pinned host buffers are stepped in place (the kernels read and write them over the
+    # host link): three steps of a trajectory, bit for bit those of device buffers (the
+    # idle-SM blocks off on both sides, as npfem_step_host runs)
+    import torch
+    cells = 6
+    p = population32(642, cells, seed=7, forces="shear", noise_pN=0.5)
+    hd = make_handle(npfem, 642, prec, tol=1e-6, fill_idle_sms=0)
+    hh = make_handle(npfem, 642, prec, tol=1e-6, fill_idle_sms=0)
+    xg, vg, sg = gpu_step_device(hd, p["x"], p["v"], p["f"], steps=3)
+    xs, vs, fs = (torch.tensor(W.to_soa(p[k]), dtype=torch.float32).pin_memory() for k in ("x", "v", "f"))
+    st = torch.zeros((cells, 32), dtype=torch.uint8).pin_memory()
+    sv = st.numpy().view(npfem.CELL_STATS_DTYPE).reshape(cells)
+    for _ in range(3):
+        hh.step_host(xs.numpy(), vs.numpy(), fs.numpy(), sv)
+    assert np.array_equal(W.from_soa(xs.double().numpy()), xg)
+    assert np.array_equal(W.from_soa(vs.double().numpy()), vg)
+    assert np.array_equal(sv["iterations"], sg["iterations"]) and (sv["status"] == 0).all()
+
+
 # ---------------------------------------------------------------------------------
 # edge cases and failure reporting (host-made failures only)
 # ---------------------------------------------------------------------------------
