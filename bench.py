@@ -14,7 +14,8 @@ the timed region on trajectories of the plain solver (other cells and seeds).
 Legs:
   value     device time of npfem_step with the state resident in HBM (CUDA events on
             the launch stream, L2 flushed between steps because the state fits in L2)
-  e2e       the same through npfem_step_host: pinned host buffers copied in and out
+  e2e       the same through npfem_step_host with pinned host buffers, which the library
+            steps in place (the kernels read and write them over the host link)
             inside the timed region
   plain     the plain FP32 GPU path (FP32 SIMT contraction, first guess y), same
             cells, steps and residual tolerance
