@@ -275,10 +275,10 @@ inline void place_vectors(GroupDesc<T>* g, int n_pad, int nt, int m, int smem_bu
 {
     const int vb = 3 * n_pad * (int)sizeof(T);
     // TRI (per-triangle rows, or per-vertex corner-gradient slots with fixed-width
-    // rings) also serves as the contraction's scratch (max(32 warps, row tiles) x 384
+    // rings) also serves as the contraction's scratch (max(32, 4 x row tiles) x 384
     // floats) and holds the warm start's normalised features ([n rounded to 16][16] floats)
     const int tri_bytes = kTriRow * nt * (int)sizeof(T);
-    const int ctr_bytes = (((n_pad + 127) / 128) > 32 ? ((n_pad + 127) / 128) : 32) * 384 * 4;
+    const int ctr_bytes = (4 * ((n_pad + 127) / 128) > 32 ? 4 * ((n_pad + 127) / 128) : 32) * 384 * 4;
     const int ws_bytes = ((n_pad + 15) & ~15) * 16 * 4;
     const int slot_bytes8 = 24 * n_pad * (int)sizeof(T);  // [8 slots][3][n_pad] corner gradients
     int tb = tri_bytes > ctr_bytes ? tri_bytes : ctr_bytes;

@@ -466,14 +466,24 @@ __device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch
     const T* __restrict__ A = Amat ? Amat : tp.ainv;
     if constexpr (sizeof(T) == 4) {
         const int ntile = (n + 127) >> 7;
-        // ntile <= nw: warp w takes tile w % ntile and a share of the j range;
-        // ntile > nw: warps loop over whole tiles.  Partials go to scratch[item][c][128].
-        const bool split = ntile <= nw;
-        for (int item = warp; item < (split ? nw : ntile); item += nw) {
-            const int tile = split ? item % ntile : item;
-            const int part = split ? item / ntile : 0;
-            const int nparts = split ? (nw - 1 - tile) / ntile + 1 : 1;
-            const int chunk = (((n + nparts - 1) / nparts) + 3) & ~3;
+        // every tile's j range in P equal parts, items (tile, part) dealt to the warps in
+        // turn; P minimises the busiest warp's columns (ceil(ntile P / nw) items of
+        // ceil(n / P) columns) within the scratch's max(32, 4 ntile) items of 384 floats.
+        // Partials go to scratch[item][c][128].
+        const int pmax = max(1, min(max(32, 4 * ntile) / ntile, n / 4));
+        int P = 1;
+        long long best = -1;
+        for (int q = 1; q <= pmax; ++q) {
+            const long long cost = (long long)((ntile * q + nw - 1) / nw) * ((((n + q - 1) / q) + 3) & ~3);
+            if (best < 0 || cost < best) {
+                best = cost;
+                P = q;
+            }
+        }
+        const int chunk = (((n + P - 1) / P) + 3) & ~3;
+        const int nitems = ntile * P;
+        for (int item = warp; item < nitems; item += nw) {
+            const int tile = item % ntile, part = item / ntile;
             const int j0 = part * chunk, j1 = min(n, j0 + chunk);
             const int row0 = tile * 128 + 4 * lane;
             float acc[3][4];
@@ -527,11 +537,7 @@ __device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch
             float s = 0.f;
             if (row < n) {
                 const int tl = row >> 7, rr = row & 127;
-                if (split) {
-                    for (int w = tl; w < nw; w += ntile) s += S[w * 384 + c * 128 + rr];
-                } else {
-                    s = S[tl * 384 + c * 128 + rr];
-                }
+                for (int it = tl; it < nitems; it += ntile) s += S[it * 384 + c * 128 + rr];
             }
             R[e] = s;
         }
