@@ -493,6 +493,31 @@ __device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch
                 for (int r = 0; r < 4; ++r) acc[c][r] = 0.f;
             if (row0 < n) {
                 int j = j0;
+                // eight columns at a time: 4 KB of A^-1 in flight per warp
+                for (; j + 8 <= j1; j += 8) {
+                    float4 av[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        av[u] = __ldg(reinterpret_cast<const float4*>(A + (size_t)(j + u) * np + row0));
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float4 x0 = *reinterpret_cast<const float4*>(Q + j + 4 * h);
+                        const float4 x1 = *reinterpret_cast<const float4*>(Q + np + j + 4 * h);
+                        const float4 x2 = *reinterpret_cast<const float4*>(Q + 2 * np + j + 4 * h);
+                        const float q0[4] = {x0.x, x0.y, x0.z, x0.w}, q1[4] = {x1.x, x1.y, x1.z, x1.w},
+                                    q2[4] = {x2.x, x2.y, x2.z, x2.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float a4[4] = {av[4 * h + u].x, av[4 * h + u].y, av[4 * h + u].z, av[4 * h + u].w};
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                acc[0][r] += a4[r] * q0[u];
+                                acc[1][r] += a4[r] * q1[u];
+                                acc[2][r] += a4[r] * q2[u];
+                            }
+                        }
+                    }
+                }
                 for (; j + 4 <= j1; j += 4) {
                     float4 av[4];
 #pragma unroll
