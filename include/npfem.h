@@ -207,8 +207,9 @@ int npfem_step(npfem_handle* const* meshes, int n_groups, const int32_t* cells_p
    array compiled into the library, held by every GPU that loads the library until
    the process exits.  Arguments, layout, results and errors are those of
    npfem_step, with these differences: every group runs the persistent SIMT solver
-   kernel (NPFEM_PREC_BF16 handles included, which then contract A^-1 in FP32 on the
-   SIMT pipes instead of the tensor-core cluster kernel), one launch per distinct
+   kernel (NPFEM_PREC_BF16 handles included, which then contract a BF16 copy of A^-1
+   with FP32 accumulation on the SIMT pipes instead of the tensor-core cluster kernel),
+   one launch per distinct
    tuned block size as npfem_step launches its SIMT groups; the temporal warm start
    (opts.warm_history) is not used; with large meshes it may run fewer persistent
    blocks so that their slots fit; and it returns INVALID_ARG when one block's

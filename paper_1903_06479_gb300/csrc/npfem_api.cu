@@ -199,6 +199,8 @@ int fill_topo(npfem_handle* h, TopoDev<T>* tp, const void* ainv, const void* min
         if ((rc = upload(h, H.L_val, &tp->l_val))) return rc;
     }
     tp->ainv_lp = nullptr;
+    tp->ainv_b16 = nullptr;
+    tp->n8 = 0;
     tp->h_ptr = nullptr;
     tp->h_idx = nullptr;
     tp->h_val = nullptr;
@@ -956,6 +958,16 @@ int npfem_create(const npfem_mesh* mesh, const npfem_material* mat, const npfem_
         h->tf.ainv_lp = abf;
         h->tf.kpad = kpad;
         h->tf.rb = rb;
+        // the SIMT contraction of a BF16 handle (meshes the clusters do not take, idle-SM
+        // blocks) reads A^-1 in BF16 too: half the bytes of FP32
+        const int n8 = (n + 7) & ~7;
+        void* asq = h->alloc<unsigned short>((size_t)n8 * n8, &e);
+        if (e) return bail(e);
+        if (publish_inverse_bf16_square(h->ainv64, n, n8, asq, 0) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            return bail(fail(NPFEM_ERR_CUDA, "publishing the BF16 A^-1 failed"));
+        h->tf.ainv_b16 = asq;
+        h->tf.n8 = n8;
         // the refinement residual q - H~ r needs H~ = ms M + (1 + beta_D/h) L
         std::vector<float> lval(h->host.L_val.size());
         for (size_t q = 0; q < lval.size(); ++q) lval[q] = (float)(lscale * h->host.L_val[q]);

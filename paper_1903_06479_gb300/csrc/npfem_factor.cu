@@ -163,6 +163,22 @@ cudaError_t publish_inverse_tf32_tiled(const double* A, int n, int tiles, int kp
     return cudaGetLastError();
 }
 
+__global__ void publish_bf16_square(const double* A, int n, int n8, __nv_bfloat16* out)
+{
+    size_t total = (size_t)n8 * n8;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(q / n8), j = (int)(q % n8);
+        out[q] = __double2bfloat16((i < n && j < n) ? A[(size_t)i * n + j] : 0.0);
+    }
+}
+
+cudaError_t publish_inverse_bf16_square(const double* A, int n, int n8, void* out, cudaStream_t s)
+{
+    publish_bf16_square<<<1024, 256, 0, s>>>(A, n, n8, static_cast<__nv_bfloat16*>(out));
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t publish_inverse_bf16_blocked(const double* A, int n, int rows_pad, int kpad, void* out, cudaStream_t s)
 {
     publish_bf16_blocked<<<1024, 256, 0, s>>>(A, n, rows_pad, kpad, (__nv_bfloat16*)out);

@@ -68,6 +68,10 @@ struct TopoDev {
     T beta_h;
     const void* ainv_lp;         // A^-1 for the tensor-core contraction: BF16 row blocks, or TF32 chunks
                                  // of 128 rows x 32 K in the MMA's core-matrix layout
+    // BF16 handles: A^-1 in BF16 (round to nearest even), [n8][n8] with n8 = n rounded up
+    // to 8 (zero padding), for the SIMT contraction's 256-row tiles (null otherwise)
+    const void* ainv_b16;
+    int n8;
     const int* h_ptr;            // L (CSR, fp32) for the refinement residual q - H~ r
     const unsigned short* h_idx;
     const float* h_val;
@@ -92,6 +96,7 @@ struct GroupDesc {
     long long stats_off;   // index of the group's first cell in stats (and eval parts)
     int cells;
     int smem_bytes;        // dynamic smem this group needs (after kFixedSmem)
+    int scratch_floats;    // size of the TRI buffer in floats (the SIMT contraction's partials)
     long long carry_off;   // element offset of the group's first carried-pairs record in LaunchArgs::carry
     long long carry_rec;   // elements per record (carry_rec_elems)
     int loc[kMaxVecs];     // >= 0: byte offset in smem; < 0: -(byte offset in the CTA's global slot) - 1
@@ -226,6 +231,8 @@ cudaError_t publish_inverse(const double* A, int n, int n_pad, float* out32, dou
 // A^-1 in BF16 as [rows_pad][kpad] (zero padding), the layout the tensor-core path
 // loads into tensor memory.
 cudaError_t publish_inverse_bf16_blocked(const double* A, int n, int rows_pad, int kpad, void* out, cudaStream_t s);
+// A^-1 in BF16 as [n8][n8] (rows and columns past n zero) for the SIMT contraction.
+cudaError_t publish_inverse_bf16_square(const double* A, int n, int n8, void* out, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_cells(const LaunchArgs<T>& a, int grid, int block, int smem, cudaStream_t s);
@@ -309,6 +316,7 @@ inline void place_vectors(GroupDesc<T>* g, int n_pad, int nt, int m, int smem_bu
         }
     }
     g->smem_bytes = base_off + used;
+    g->scratch_floats = tb / 4;
     *slot_bytes = gl;
 }
 

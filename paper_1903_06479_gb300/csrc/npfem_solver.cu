@@ -459,12 +459,102 @@ __device__ void evaluate(const TopoDev<T>& tp, const T* XN, const T* U, const T*
 // triangle buffer, idle outside the objective evaluation) and are added in a fixed
 // order, so the result is deterministic.
 template <typename T>
-__device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch, const T* Amat = nullptr)
+__device__ void contract_simt(const TopoDev<T>& tp, const T* Q, T* R, T* scratch, const T* Amat = nullptr,
+                              int scratch_floats = 0)
 {
     const int n = tp.n, np = tp.n_pad, N3 = 3 * np;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const T* __restrict__ A = Amat ? Amat : tp.ainv;
     if constexpr (sizeof(T) == 4) {
+        if (!Amat && tp.ainv_b16) {
+            // BF16 A^-1 (a BF16 handle), FP32 accumulation: 256-row tiles, each lane 8
+            // consecutive rows of a column in one 16-byte load; the same balanced split of
+            // the columns into parts as below, bounded by the scratch's size
+            const unsigned short* __restrict__ Ab = static_cast<const unsigned short*>(tp.ainv_b16);
+            const int n8 = tp.n8;
+            const int ntile = (n + 255) >> 8;
+            const int cap = scratch_floats > 0 ? scratch_floats / 768 : max(32, 4 * ((n + 127) >> 7)) / 2;
+            const int pmax = max(1, min(cap / ntile, n / 4));
+            int P = 1;
+            long long best = -1;
+            for (int q = 1; q <= pmax; ++q) {
+                const long long cost = (long long)((ntile * q + nw - 1) / nw) * ((((n + q - 1) / q) + 3) & ~3);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    P = q;
+                }
+            }
+            const int chunk = (((n + P - 1) / P) + 3) & ~3;
+            const int nitems = ntile * P;
+            for (int item = warp; item < nitems; item += nw) {
+                const int tile = item % ntile, part = item / ntile;
+                const int j0 = part * chunk, j1 = min(n, j0 + chunk);
+                const int row0 = tile * 256 + 8 * lane;
+                float acc[3][8];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) acc[c][r] = 0.f;
+                if (row0 < n) {
+                    int j = j0;
+                    for (; j + 4 <= j1; j += 4) {
+                        uint4 av[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            av[u] = __ldg(reinterpret_cast<const uint4*>(Ab + (size_t)(j + u) * n8 + row0));
+                        const float4 x0 = *reinterpret_cast<const float4*>(Q + j);
+                        const float4 x1 = *reinterpret_cast<const float4*>(Q + np + j);
+                        const float4 x2 = *reinterpret_cast<const float4*>(Q + 2 * np + j);
+                        const float q0[4] = {x0.x, x0.y, x0.z, x0.w}, q1[4] = {x1.x, x1.y, x1.z, x1.w},
+                                    q2[4] = {x2.x, x2.y, x2.z, x2.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const unsigned w[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) {
+                                // BF16 to FP32: the 16 bits are the float's high half
+                                const float a = __uint_as_float((r & 1) ? (w[r >> 1] & 0xffff0000u) : (w[r >> 1] << 16));
+                                acc[0][r] += a * q0[u];
+                                acc[1][r] += a * q1[u];
+                                acc[2][r] += a * q2[u];
+                            }
+                        }
+                    }
+                    for (; j < j1; ++j) {
+                        const uint4 a4 = __ldg(reinterpret_cast<const uint4*>(Ab + (size_t)j * n8 + row0));
+                        const unsigned w[4] = {a4.x, a4.y, a4.z, a4.w};
+                        const float qq[3] = {Q[j], Q[np + j], Q[2 * np + j]};
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            const float a = __uint_as_float((r & 1) ? (w[r >> 1] & 0xffff0000u) : (w[r >> 1] << 16));
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) acc[c][r] += a * qq[c];
+                        }
+                    }
+                }
+                float* Pp = reinterpret_cast<float*>(scratch) + item * 768;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    *reinterpret_cast<float4*>(Pp + c * 256 + 8 * lane) =
+                        make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+                    *reinterpret_cast<float4*>(Pp + c * 256 + 8 * lane + 4) =
+                        make_float4(acc[c][4], acc[c][5], acc[c][6], acc[c][7]);
+                }
+            }
+            __syncthreads();
+            const float* Sb = reinterpret_cast<const float*>(scratch);
+            for (int e = threadIdx.x; e < N3; e += blockDim.x) {
+                const int c = e / np, row = e - c * np;
+                float sum = 0.f;
+                if (row < n) {
+                    const int tl = row >> 8, rr = row & 255;
+                    for (int it = tl; it < nitems; it += ntile) sum += Sb[it * 768 + c * 256 + rr];
+                }
+                R[e] = sum;
+            }
+            __syncthreads();
+            return;
+        }
         const int ntile = (n + 127) >> 7;
         // every tile's j range in P equal parts, items (tile, part) dealt to the warps in
         // turn; P minimises the busiest warp's columns (ceil(ntile P / nw) items of
@@ -1835,7 +1925,7 @@ __device__ __forceinline__ void contract_any(const LaunchArgs<T>& a, const TopoD
             return;
         }
     }
-    contract_simt(tp, Q, R, S.TRIv);
+    contract_simt(tp, Q, R, S.TRIv, static_cast<const T*>(nullptr), S.gd->scratch_floats);
 }
 
 template <typename T, int MAXT>
