@@ -92,7 +92,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--legs", default="all", help="extra workload legs: all, none, or a comma list of regen, "
-                    "refine1, c4, c4_tf32, c4_bf16_refine1, c3")
+                    "refine1, c4, c4_tf32, c4_bf16_refine1, c3 (all), and tnet (the temporal network's ablation, "
+                    "only when named)")
     ap.add_argument("--force-noise-regen", type=int, default=0,
                     help="1: the N(0, 0.5 pN) force noise is redrawn every step (4 draws used in turn, copied in "
                          "outside the step's events); 0: the force is fixed over the run")
@@ -498,6 +499,50 @@ def compare_leg(N, W, torch, name, pops, counts, args, flush, ws_params, local, 
     return out
 
 
+def tnet_leg(N, W, torch, local, rank, cells):
+    """The temporal network against the temporal warm start alone: iterations per cell and
+    step time of the headline cells over steps 6-25 from rest (BF16, warm_history 1), on
+    both force recipes, one network per recipe trained by the library's kernels on 500
+    other cells stepped 60 times with that recipe (learn.train_temporal_warmstart)."""
+    from paper_1903_06479_gb300 import learn
+    rest, tris = W.discocyte(N_VERTS)
+    pop = W.population(N_VERTS, cells, seed=1 + rank, forces="shear", noise_pN=0.5)
+    mk = lambda a: torch.tensor(W.to_soa(a), dtype=torch.float32, device="cuda")
+    out = {}
+    for recipe, frac in (("fixed", 0.0), ("regen", 1.0)):
+        hb = N.Handle(rest, tris, N.material(), N.default_opts(precision="fp32"), dt=DT, device=local)
+        t0 = time.perf_counter()
+        P, info = learn.train_temporal_warmstart(hb, n_cells=500, steps=60, seed=300 + rank, train_steps=50000,
+                                                 regen_fraction=frac)
+        row = {"train_s": time.perf_counter() - t0, "loss_init": info["loss_init"], "loss_final": info["loss_final"]}
+        for net in (False, True):
+            h = N.Handle(rest, tris, N.material(), N.default_opts(precision="bf16", tol=1e-6, warm_history=1), dt=DT,
+                         device=local)
+            if net:
+                h.set_warmstart_temporal(P.astype(np.float32))
+            x, v, f, fs = mk(pop["x"]), mk(pop["v"]), mk(pop["f"]), mk(pop["f_shear"])
+            g = torch.Generator(device="cuda")
+            g.manual_seed(5)
+            st = torch.zeros((cells, 32), dtype=torch.uint8, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            its, ms = [], []
+            for k in range(25):
+                if recipe == "regen":
+                    f.copy_(fs + 0.5 * torch.randn(fs.shape, device="cuda", generator=g))
+                e0.record()
+                N.step([h], [cells], x, v, f, DT, stats=st)
+                e1.record()
+                torch.cuda.synchronize()
+                s = st.cpu().numpy().view(N.CELL_STATS_DTYPE).reshape(cells)
+                if k >= 5:
+                    its.append(float(s["iterations"].mean()))
+                    ms.append(e0.elapsed_time(e1))
+            row["with_network" if net else "temporal_only"] = {"iterations_per_cell": float(np.mean(its)),
+                                                                "ms_per_step": float(np.mean(ms))}
+        out[recipe] = row
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -613,6 +658,8 @@ def main():
             legs["c4_bf16_refine1"]["form"] = "BF16 tensor-core A^-1 contraction (clusters) + one refinement sweep"
             legs["c4_bf16_refine1"]["workload"] = w4
         del p4
+    if "tnet" in want:
+        legs["tnet"] = tnet_leg(N, W, torch, local, rank, cells)
     if "c3" in want:
         n_all = 4096
         c258, c642 = round(0.4 * n_all), round(0.4 * n_all)
